@@ -1,0 +1,223 @@
+/*
+ * st.h — C ABI of the GB300 synthetic-tracking (shift-and-stack) library.
+ *
+ * Method (Burdanov, Hasler & de Wit 2023, "GPU-based framework for detecting
+ * small Solar System bodies in targeted exoplanet surveys"):
+ *   Sec. 1   shift-and-stack: remove stationary sources, predict a linear
+ *            motion, shift each image along it and combine the shifted images;
+ *            synthetic tracking repeats this over a blind grid of motions.
+ *   Sec. 2.1 (Last-night data) the frames are shifted and summed with no
+ *            constraint on position angle, assuming linear motion; the
+ *            slowest motion is set by the minimum shift (about 0.5 px); the
+ *            output is a set of tracks with speed, position angle, pixel
+ *            coordinates and S/N; an object must stand above the threshold
+ *            in at least half of the images.
+ *
+ * Everything below runs on one CUDA device.  All pointers named d_* are
+ * device pointers and h_* are host pointers.  The caller owns every buffer it
+ * passes in; the plan owns its own workspace.  No call throws: each returns an
+ * st_status, and st_last_error() gives a message for the calling thread.
+ *
+ * Definitions shared by every entry point (the library's reading of Sec. 2.1):
+ *   dt_i      = t_i - t_ref, in FP64.
+ *   v(a,b)    = (vx0 + a*dvx, vy0 + b*dvy), a in [0,nvx), b in [0,nvy);
+ *               linear velocity index k = b*nvx + a.
+ *   nearest   : sx(i,a) = floor(vx_a*dt_i + 0.5), sy(i,b) likewise, FP64,
+ *               no fused multiply-add.
+ *   stack     : S_k(x,y) = sum_{i=0..N-1} I_i(x+sx(i,a), y+sy(i,b)), the sum
+ *               taken in FP32 in frame order i = 0..N-1 with one accumulator;
+ *               samples outside the frame contribute +0.0.
+ *   coverage  : n_cov(x,y,k) = number of frames whose sample is inside.
+ *   bilinear  : the shift s = v*dt_i is split into floor(s) and a fraction f;
+ *               the sample interpolates the four taps around x+floor(s) with
+ *               weights (1-fx, fx) x (1-fy, fy); taps outside read 0; the
+ *               sample is inside iff 0 <= x+s <= W-1 and 0 <= y+s_y <= H-1.
+ *   candidate : n_cov >= n_min (n_min = ceil(N/2) unless given), and
+ *               S >= thr[n_cov] with thr[n] = (float)(tau*sqrt((double)n)),
+ *               and S is a local maximum of S_k over its 8 neighbours inside
+ *               the frame whose n_cov >= n_min: strictly greater than the
+ *               neighbours that come earlier in raster order (y, then x) and
+ *               greater or equal to the later ones.
+ *   snr       : S * (float)(1/sqrt((double)n_cov)), in FP32.
+ *   order     : candidates are returned sorted by (field, k, y, x).
+ */
+#ifndef ST_H_
+#define ST_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ST_VERSION_MAJOR 0
+#define ST_VERSION_MINOR 1
+
+typedef enum {
+  ST_OK = 0,
+  ST_ERR_INVALID = 1,     /* an argument is out of range; nothing was launched */
+  ST_ERR_CUDA = 2,        /* a CUDA runtime call failed; message has the CUDA error */
+  ST_ERR_OOM = 3,         /* device or pinned-host allocation failed; nothing leaked */
+  ST_ERR_OVERFLOW = 4,    /* more candidates than capacity; *h_count holds the true count */
+  ST_ERR_TIMEOUT = 5,     /* a bounded device wait ran out; the device stays usable */
+  ST_ERR_UNSUPPORTED = 6  /* valid request this build does not implement */
+} st_status;
+
+typedef enum { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2 } st_dtype;
+typedef enum { ST_NEAREST = 0, ST_BILINEAR = 1 } st_shift;
+
+/* One field: a cube of n_frames frames of width x height pixels, row-major
+ * [n_frames][height][width], and the velocity grid searched over it.
+ * Velocities are in pixels per unit of the timestamps. */
+typedef struct {
+  int32_t width, height, n_frames;
+  double t_ref;              /* reference epoch; same unit as the timestamps */
+  double vx0, dvx;           /* x velocity grid: vx_a = vx0 + a*dvx */
+  int32_t nvx;
+  double vy0, dvy;           /* y velocity grid: vy_b = vy0 + b*dvy */
+  int32_t nvy;
+  float snr_threshold;       /* tau, in units of the per-frame noise sigma */
+  int32_t min_coverage;      /* n_min; 0 selects ceil(n_frames/2) (Sec. 2.1) */
+} st_field;
+
+typedef struct {
+  st_dtype storage;          /* frame storage type on the device; sums are always FP32 */
+  st_shift mode;             /* ST_NEAREST or ST_BILINEAR */
+  int32_t normalize;         /* 1: per-frame robust sky mean/sigma in FP64 and
+                                I = (R - mu)/sigma, NaN -> 0; 0: frames are used
+                                as given (NaN propagates) */
+  float cr_clip;             /* with normalize: zero |I| > cr_clip; 0 disables */
+  int32_t use_graph;         /* 1: capture the search of all fields into a CUDA
+                                graph on the first call and replay it later */
+  int32_t tile;              /* stack kernel tile variant; -1 = autotune, 0 = plan default */
+  const char* tune_cache;    /* JSON file for autotuned tiles, or NULL */
+  int64_t pending_capacity;  /* above-threshold points held before the local-max
+                                test; 0 selects a default of 4 Mi points */
+} st_opts;
+
+/* One detection (Sec. 2.1: pixel coordinates, velocity and S/N). 28 bytes. */
+typedef struct {
+  int32_t x, y;              /* pixel in reference-epoch coordinates */
+  int32_t k;                 /* velocity index, k = b*nvx + a */
+  int32_t field;             /* index of the field in the plan */
+  float stack;               /* S_k(x, y) */
+  float snr;                 /* S * (1/sqrt(n_cov)) */
+  int32_t n_cov;             /* frames covering the pixel */
+} st_candidate;
+
+/* One refined detection: continuous motion and position at t_ref. */
+typedef struct {
+  float vx, vy, x0, y0, flux;
+  float snr;                 /* matched-filter S/N at the final parameters */
+  float obj;                 /* objective J at the final parameters */
+  int32_t field;
+} st_refined;
+
+typedef struct st_plan_s st_plan_t;
+
+/* Library version as MAJOR*100 + MINOR. */
+int32_t st_version(void);
+
+/* Message of the last failing call on this thread; valid until the next call
+ * on the same thread.  Never NULL. */
+const char* st_last_error(void);
+
+/* Builds a plan for n_fields fields: validates them, sizes the workspace,
+ * allocates it on the current device and picks the stack tile variant.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream) on which every
+ * later call on this plan is ordered.  Limits: width, height <= 16384,
+ * n_frames <= 65536, nvx*nvy <= 2^26, n_fields <= 255.  On failure *out is
+ * NULL and nothing is left allocated. */
+st_status st_plan(const st_field* fields, int32_t n_fields, const st_opts* opts,
+                  void* cuda_stream, st_plan_t** out);
+
+/* Releases the plan and its workspace.  NULL-safe. Synchronises the plan's stream. */
+void st_free(st_plan_t* plan);
+
+/* The search of Sec. 2.1 over every field of the plan: shift tables, optional
+ * normalisation, shift-and-stack over the whole grid, threshold, local maxima,
+ * and the sorted candidate list.
+ *   d_frames[f]: device FP32 cube of field f, [N][H][W] row-major, read-only.
+ *   h_times[f] : host FP64 timestamps of field f, [N].
+ *   d_out      : device array of `capacity` candidates (may be NULL if capacity 0).
+ *   h_count    : receives the total number of candidates found.
+ * Synchronises the plan's stream (to read the count).  Returns ST_ERR_OVERFLOW
+ * when the total exceeds capacity: the first `capacity` records of the sorted
+ * list are written and *h_count holds the total, so a retry with a larger
+ * buffer succeeds.  Returns ST_ERR_OVERFLOW with *h_count = -1 when the
+ * above-threshold points exceed the plan's pending_capacity. */
+st_status st_stack_search(st_plan_t* plan, const float* const* d_frames,
+                          const double* const* h_times, st_candidate* d_out,
+                          int64_t capacity, int64_t* h_count);
+
+/* Same search with host buffers: h_frames[f] are host FP32 cubes (pinned or
+ * pageable) copied to the device inside the call, and the sorted candidates
+ * are copied back into h_out (capacity records).  The plan holds the device
+ * copies, allocated on the first call. */
+st_status st_stack_search_host(st_plan_t* plan, const float* const* h_frames,
+                               const double* const* h_times, st_candidate* h_out,
+                               int64_t capacity, int64_t* h_count);
+
+/* Differentiable refinement of candidates (not in the paper; a continuous
+ * refinement of grid detections).  For each input candidate of field f the
+ * parameters theta = (vx, vy, x0, y0, F) start at the grid velocity, the pixel
+ * and F = S/(N<g,g>); the objective on a 64x64 output cutout centred on the
+ * starting pixel is
+ *     J = F*<g, S_theta> - 0.5*F^2*N_cov*<g, g>,
+ * with S_theta the bilinear stack of the raw cube (FP32 input frames of the
+ * plan's last search, normalised when the plan normalises) and g a Gaussian
+ * of the given FWHM centred on (x0, y0).  `steps` optimiser steps
+ * (optimizer 0 = Adam, lr_pos px for x0, y0 and lr_vel for vx, vy) maximise J.
+ * d_in: device candidates; d_out: device results [n]; d_grad_out: optional
+ * device [n][5] gradient dJ/dtheta at the final parameters (order vx, vy, x0,
+ * y0, F).  Requires a prior st_stack_search on the plan (frames resident). */
+st_status st_refine(st_plan_t* plan, const st_candidate* d_in, int64_t n,
+                    int32_t steps, int32_t optimizer, float fwhm, float lr_pos,
+                    float lr_vel, st_refined* d_out, float* d_grad_out);
+
+/* Forward and adjoint of the refinement objective for explicit parameters, the
+ * building block of the autograd binding.  theta: device [n][5] (vx, vy, x0,
+ * y0, F); centre: device [n][2] int32 cutout centres; fields: device [n]
+ * int32.  Writes J [n], SNR [n] and, if d_grad is not NULL, dJ/dtheta [n][5].
+ * Frames are those of the plan's last search. */
+st_status st_refine_eval(st_plan_t* plan, const float* d_theta,
+                         const int32_t* d_centre, const int32_t* d_field,
+                         int64_t n, float fwhm, float* d_J, float* d_snr,
+                         float* d_grad);
+
+/* Diagnostics used by the tests. */
+
+/* Shift tables of field f for timestamps h_times: h_sx [N][nvx], h_sy [N][nvy]
+ * (nearest mode: the rounded shifts; bilinear: floor of the shift) and, if
+ * not NULL, h_fx [N][nvx], h_fy [N][nvy] the FP32 fractions.  Computed by the
+ * device kernel of the search. */
+st_status st_shift_tables(st_plan_t* plan, int32_t field, const double* h_times,
+                          int32_t* h_sx, int32_t* h_sy, float* h_fx, float* h_fy);
+
+/* Robust sky statistics and normalisation alone (field f):  d_frames as in
+ * st_stack_search; writes the storage cube into d_cube (device, N*H*W elements
+ * of the plan's storage type) and per-frame h_mu, h_sigma (host, [N]). */
+st_status st_normalize(st_plan_t* plan, int32_t field, const float* d_frames,
+                       void* d_cube, double* h_mu, double* h_sigma);
+
+/* Full stack planes S_k and n_cov for the n_k velocity indices h_k of field f,
+ * computed by the search kernel: d_S [n_k][H][W] FP32, d_ncov [n_k][H][W]
+ * int32 (may be NULL).  Frames are processed exactly as by st_stack_search. */
+st_status st_dump_stack(st_plan_t* plan, int32_t field, const float* d_frames,
+                        const double* h_times, const int32_t* h_k, int32_t n_k,
+                        float* d_S, int32_t* d_ncov);
+
+/* Number of the library's own kernel launches issued by the last
+ * st_stack_search / st_stack_search_host / st_refine call on this plan. */
+int64_t st_last_launch_count(const st_plan_t* plan);
+
+/* Average device time in milliseconds of the main stack kernel over the last
+ * search call (CUDA events on the plan's stream), and its launch count. */
+st_status st_last_stack_kernel_time(const st_plan_t* plan, double* ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ST_H_ */

@@ -1,0 +1,164 @@
+"""CPU oracle of the synthetic-tracking search (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It is a ctypes wrapper around
+``oracle.c`` (and ``refine_oracle.c``), a plain FP64 / FP32-sequential
+restatement of the method of Burdanov, Hasler & de Wit (2023), Sec. 1 and
+Sec. 2.1; it shares no code with the CUDA library.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+class OracleCand(C.Structure):
+    _fields_ = [("x", C.c_int32), ("y", C.c_int32), ("k", C.c_int32), ("n_cov", C.c_int32),
+                ("stack", C.c_double), ("snr", C.c_double)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        P = C.c_void_p
+        L.oracle_shift_tables.argtypes = [P, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int,
+                                          C.c_int, P, P]
+        L.oracle_sky_stats.argtypes = [P, C.c_int64, C.c_double, C.c_int, P, P, P, P]
+        L.oracle_normalize.argtypes = [P, C.c_int, C.c_int64, C.c_double, C.c_int, C.c_float, P,
+                                       P, P]
+        L.oracle_round_bf16.argtypes = [P, C.c_int64, P]
+        grid = [C.c_double, C.c_double, C.c_double, C.c_int, C.c_double, C.c_double, C.c_int]
+        L.oracle_stack_planes.argtypes = [P, C.c_int, C.c_int, C.c_int, P] + grid + [
+            C.c_int, C.c_int, P, C.c_int, P, P]
+        L.oracle_stack_points.argtypes = [P, C.c_int, C.c_int, C.c_int, P] + grid + [
+            C.c_int, C.c_int, P, C.c_int64, P, P]
+        L.oracle_search.argtypes = [P, C.c_int, C.c_int, C.c_int, P] + grid + [
+            C.c_int, C.c_int, C.c_float, C.c_int, C.c_int32, C.c_int32, P, C.c_int64]
+        L.oracle_search.restype = C.c_int64
+        L.oracle_num_threads.restype = C.c_int
+        if hasattr(L, "oracle_refine_eval"):
+            L.oracle_refine_eval.argtypes = [P, C.c_int, C.c_int, C.c_int, P, C.c_double, P, P,
+                                             C.c_int64, C.c_double, P, P, P]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def num_threads() -> int:
+    return lib().oracle_num_threads()
+
+
+def shift_tables(t, t_ref, v0, dv, nv, mode="nearest"):
+    """Shift table [N][nv] (int32) and fractions [N][nv] (FP64)."""
+    t = _f64(t)
+    s = np.zeros((t.size, nv), np.int32)
+    f = np.zeros((t.size, nv), np.float64)
+    lib().oracle_shift_tables(_p(t), t.size, t_ref, v0, dv, nv, 0 if mode == "nearest" else 1,
+                              _p(s), _p(f))
+    return s, f
+
+
+def sky_stats(frame, kappa=3.0, max_iter=5):
+    x = _f32(frame).ravel()
+    mu = C.c_double()
+    sd = C.c_double()
+    kept = C.c_int64()
+    it = C.c_int()
+    lib().oracle_sky_stats(_p(x), x.size, kappa, max_iter, C.byref(mu), C.byref(sd),
+                           C.byref(kept), C.byref(it))
+    return mu.value, sd.value, kept.value, it.value
+
+
+def normalize(raw, kappa=3.0, max_iter=5, cr_clip=0.0):
+    raw = _f32(raw)
+    N = raw.shape[0]
+    npix = raw[0].size
+    out = np.empty_like(raw)
+    mu = np.zeros(N)
+    sd = np.zeros(N)
+    lib().oracle_normalize(_p(raw), N, npix, kappa, max_iter, cr_clip, _p(out), _p(mu), _p(sd))
+    return out, mu, sd
+
+
+def round_bf16(x):
+    x = _f32(x)
+    out = np.empty_like(x)
+    lib().oracle_round_bf16(_p(x), x.size, _p(out))
+    return out
+
+
+def _grid(field):
+    return (float(field["t_ref"]), float(field["vx0"]), float(field["dvx"]), int(field["nvx"]),
+            float(field["vy0"]), float(field["dvy"]), int(field["nvy"]))
+
+
+def stack_planes(frames, t, field, ks, mode="nearest", prec="fp64"):
+    """S [len(ks)][H][W] (float64 holding FP32 values in 'fp32' mode) and n_cov."""
+    frames = _f32(frames)
+    t = _f64(t)
+    N, H, W = frames.shape
+    ks = np.ascontiguousarray(ks, dtype=np.int32)
+    S = np.zeros((ks.size, H, W), np.float64)
+    Cv = np.zeros((ks.size, H, W), np.int32)
+    lib().oracle_stack_planes(_p(frames), N, H, W, _p(t), *_grid(field),
+                              0 if mode == "nearest" else 1, 0 if prec == "fp64" else 1,
+                              _p(ks), ks.size, _p(S), _p(Cv))
+    return S, Cv
+
+
+def stack_points(frames, t, field, xyk, mode="nearest", prec="fp64"):
+    frames = _f32(frames)
+    t = _f64(t)
+    N, H, W = frames.shape
+    xyk = np.ascontiguousarray(xyk, dtype=np.int32).reshape(-1, 3)
+    S = np.zeros(len(xyk), np.float64)
+    Cv = np.zeros(len(xyk), np.int32)
+    lib().oracle_stack_points(_p(frames), N, H, W, _p(t), *_grid(field),
+                              0 if mode == "nearest" else 1, 0 if prec == "fp64" else 1,
+                              _p(xyk), len(xyk), _p(S), _p(Cv))
+    return S, Cv
+
+
+def search(frames, t, field, mode="nearest", prec="fp32", k_begin=0, k_end=None, cap=None):
+    """Sorted candidates as a structured numpy array (x, y, k, n_cov, stack, snr)."""
+    frames = _f32(frames)
+    t = _f64(t)
+    N, H, W = frames.shape
+    nk = int(field["nvx"]) * int(field["nvy"])
+    if k_end is None:
+        k_end = nk
+    args = (_p(frames), N, H, W, _p(t), *_grid(field), 0 if mode == "nearest" else 1,
+            0 if prec == "fp64" else 1, float(field["snr_threshold"]),
+            int(field.get("min_coverage", 0)), int(k_begin), int(k_end))
+    L = lib()
+    explicit = cap is not None
+    cap = cap if explicit else 1 << 18
+    buf = (OracleCand * max(cap, 1))()
+    n = L.oracle_search(*args, C.cast(buf, C.c_void_p), cap)
+    if n < 0:
+        raise MemoryError("oracle_search allocation failed")
+    if n > cap and not explicit:
+        cap = n
+        buf = (OracleCand * cap)()
+        n = L.oracle_search(*args, C.cast(buf, C.c_void_p), cap)
+    dt = np.dtype([("x", np.int32), ("y", np.int32), ("k", np.int32), ("n_cov", np.int32),
+                   ("stack", np.float64), ("snr", np.float64)])
+    arr = np.frombuffer(bytearray(buf), dtype=dt, count=min(n, cap)).copy()
+    return arr
