@@ -1,0 +1,484 @@
+// st_api.cu — the C ABI of include/st.h: plan, search, diagnostics.
+//
+// The search of Sec. 2.1 (Burdanov, Hasler & de Wit 2023) runs as:
+//   shift tables (FP64 dt_i = t_i - t_ref)  ->  optional robust normalisation
+//   ->  shift-and-stack + threshold (stack kernels)  ->  local maxima
+//   ->  sort by (field, k, y, x)  ->  caller's buffer.
+// Every step is a kernel of this library; the host only validates, sizes
+// workspace, launches and reads the candidate count.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "st_internal.h"
+
+using namespace st;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+st_status fail(st_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      if (e_ == cudaErrorMemoryAllocation)                                            \
+        return fail(ST_ERR_OOM, "%s: %s", #call, cudaGetErrorString(e_));             \
+      return fail(ST_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));              \
+    }                                                                                 \
+  } while (0)
+
+int64_t pow2_at_least(int64_t n) {
+  int64_t p = 1;
+  while (p < n) p <<= 1;
+  return p;
+}
+
+}  // namespace
+
+struct FieldPlan {
+  st_field f{};
+  int nmin = 0;
+  double* d_t = nullptr;
+  int32_t* d_sx = nullptr;
+  int32_t* d_sy = nullptr;
+  float* d_fx = nullptr;
+  float* d_fy = nullptr;
+  float* d_thr = nullptr;
+  float* d_rsq = nullptr;
+  void* d_cube = nullptr;        // normalised / converted storage cube (owned)
+  float* d_frames_copy = nullptr; // device copy for the host-buffer entry point
+  FastPlan* fast = nullptr;
+  bool fast_checked = false;
+  const float* last_frames = nullptr;
+  int64_t P() const { return (int64_t)f.width * f.height; }
+  int64_t nk() const { return (int64_t)f.nvx * f.nvy; }
+};
+
+struct st_plan_s {
+  std::vector<FieldPlan> F;
+  st_opts o{};
+  cudaStream_t s = nullptr;
+  int device = 0;
+  Pending* d_pend = nullptr;
+  int64_t pend_cap = 0;
+  Counters* d_ctr = nullptr;
+  Counters* h_ctr = nullptr;  // pinned
+  st_candidate* d_cand = nullptr;
+  uint64_t* d_keys = nullptr;
+  uint32_t* d_idx = nullptr;
+  int64_t sort_cap = 0;
+  FieldDev* d_fds = nullptr;
+  double* d_sky = nullptr;
+  st_candidate* d_hout = nullptr;
+  int64_t hout_cap = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  double stack_ms = 0.0;
+  int64_t stack_launches = 0;
+  int64_t launches = 0;
+  bool has_search = false;
+};
+
+namespace {
+
+void free_plan(st_plan_t* p) {
+  if (!p) return;
+  if (p->s) cudaStreamSynchronize(p->s);
+  for (auto& fp : p->F) {
+    cudaFree(fp.d_t);
+    cudaFree(fp.d_sx);
+    cudaFree(fp.d_sy);
+    cudaFree(fp.d_fx);
+    cudaFree(fp.d_fy);
+    cudaFree(fp.d_thr);
+    cudaFree(fp.d_rsq);
+    cudaFree(fp.d_cube);
+    cudaFree(fp.d_frames_copy);
+    if (fp.fast) fast_plan_free(fp.fast);
+  }
+  cudaFree(p->d_pend);
+  cudaFree(p->d_ctr);
+  if (p->h_ctr) cudaFreeHost(p->h_ctr);
+  cudaFree(p->d_cand);
+  cudaFree(p->d_keys);
+  cudaFree(p->d_idx);
+  cudaFree(p->d_fds);
+  cudaFree(p->d_sky);
+  cudaFree(p->d_hout);
+  if (p->e0) cudaEventDestroy(p->e0);
+  if (p->e1) cudaEventDestroy(p->e1);
+  delete p;
+}
+
+st_status validate_field(const st_field& f, int idx) {
+  if (f.width <= 0 || f.height <= 0 || f.width > 16384 || f.height > 16384)
+    return fail(ST_ERR_INVALID, "field %d: width/height must be in [1, 16384]", idx);
+  if (f.n_frames <= 0 || f.n_frames > 65536)
+    return fail(ST_ERR_INVALID, "field %d: n_frames must be in [1, 65536]", idx);
+  if (f.nvx <= 0 || f.nvy <= 0 || (int64_t)f.nvx * f.nvy > (1ll << 26))
+    return fail(ST_ERR_INVALID, "field %d: nvx, nvy >= 1 and nvx*nvy <= 2^26", idx);
+  if (!std::isfinite(f.t_ref) || !std::isfinite(f.vx0) || !std::isfinite(f.dvx) ||
+      !std::isfinite(f.vy0) || !std::isfinite(f.dvy))
+    return fail(ST_ERR_INVALID, "field %d: grid and t_ref must be finite", idx);
+  if (!std::isfinite(f.snr_threshold) || f.snr_threshold < 0.0f)
+    return fail(ST_ERR_INVALID, "field %d: snr_threshold must be finite and >= 0", idx);
+  if (f.min_coverage < 0 || f.min_coverage > f.n_frames)
+    return fail(ST_ERR_INVALID, "field %d: min_coverage must be in [0, n_frames]", idx);
+  return ST_OK;
+}
+
+st_status check_times(const double* t, int N, const st_field& f, int idx) {
+  if (!t) return fail(ST_ERR_INVALID, "field %d: timestamps are NULL", idx);
+  for (int i = 0; i < N; ++i)
+    if (!std::isfinite(t[i])) return fail(ST_ERR_INVALID, "field %d: timestamp %d not finite", idx, i);
+  // |v * dt| must stay inside int32 shifts
+  double vmax = std::max(std::max(std::fabs(f.vx0), std::fabs(f.vx0 + (f.nvx - 1) * f.dvx)),
+                         std::max(std::fabs(f.vy0), std::fabs(f.vy0 + (f.nvy - 1) * f.dvy)));
+  for (int i = 0; i < N; ++i)
+    if (vmax * std::fabs(t[i] - f.t_ref) > 1e9)
+      return fail(ST_ERR_INVALID, "field %d: shift of frame %d exceeds 1e9 px", idx, i);
+  return ST_OK;
+}
+
+size_t store_bytes(int storage) { return storage == ST_F32 ? 4 : 2; }
+
+// Tables + optional normalisation for field fi with the given frames/times.
+st_status prepare_field(st_plan_t* p, int fi, const float* d_frames, const double* h_times,
+                        int64_t* launches) {
+  FieldPlan& fp = p->F[fi];
+  const st_field& f = fp.f;
+  st_status st = check_times(h_times, f.n_frames, f, fi);
+  if (st != ST_OK) return st;
+  CK(cudaMemcpyAsync(fp.d_t, h_times, sizeof(double) * f.n_frames, cudaMemcpyHostToDevice, p->s));
+  *launches += launch_shift_tables(fp.d_t, f.n_frames, f.t_ref, f.vx0, f.dvx, f.nvx, f.vy0, f.dvy,
+                                   f.nvy, p->o.mode, fp.d_sx, fp.d_sy, fp.d_fx, fp.d_fy, p->s);
+  if (fp.d_cube) {
+    *launches += launch_normalize(d_frames, f.n_frames, fp.P(), p->o.normalize, p->o.cr_clip,
+                                  p->o.storage, fp.d_cube, nullptr, nullptr, p->d_sky, p->s);
+  }
+  fp.last_frames = d_frames;
+  CK(cudaGetLastError());
+  return ST_OK;
+}
+
+FieldDev field_dev(const FieldPlan& fp, const float* d_frames, int fi, int storage) {
+  FieldDev d{};
+  d.cube = fp.d_cube ? fp.d_cube : (const void*)d_frames;
+  d.storage = fp.d_cube ? storage : ST_F32;
+  d.W = fp.f.width;
+  d.H = fp.f.height;
+  d.N = fp.f.n_frames;
+  d.nvx = fp.f.nvx;
+  d.nvy = fp.f.nvy;
+  d.nmin = fp.nmin;
+  d.field = fi;
+  d.sx = fp.d_sx;
+  d.sy = fp.d_sy;
+  d.fx = fp.d_fx;
+  d.fy = fp.d_fy;
+  d.thr = fp.d_thr;
+  d.rsq = fp.d_rsq;
+  return d;
+}
+
+st_status device_search(st_plan_t* p, const float* const* d_frames, const double* const* h_times,
+                        st_candidate* d_out, int64_t capacity, int64_t* h_count) {
+  if (!d_frames || !h_times || !h_count) return fail(ST_ERR_INVALID, "NULL argument");
+  if (capacity < 0 || (capacity > 0 && !d_out))
+    return fail(ST_ERR_INVALID, "capacity must be >= 0 and d_out non-NULL when capacity > 0");
+  int nf = (int)p->F.size();
+  for (int fi = 0; fi < nf; ++fi)
+    if (!d_frames[fi]) return fail(ST_ERR_INVALID, "field %d: frames are NULL", fi);
+  int64_t L = 0;
+  std::vector<FieldDev> fds(nf);
+  for (int fi = 0; fi < nf; ++fi) {
+    st_status st = prepare_field(p, fi, d_frames[fi], h_times[fi], &L);
+    if (st != ST_OK) return st;
+    fds[fi] = field_dev(p->F[fi], d_frames[fi], fi, p->o.storage);
+  }
+  CK(cudaMemcpyAsync(p->d_fds, fds.data(), sizeof(FieldDev) * nf, cudaMemcpyHostToDevice, p->s));
+  CK(cudaMemsetAsync(p->d_ctr, 0, sizeof(Counters), p->s));
+  CK(cudaEventRecord(p->e0, p->s));
+  int64_t stack_launches = 0;
+  for (int fi = 0; fi < nf; ++fi) {
+    FieldPlan& fp = p->F[fi];
+    int n = launch_stack_generic(fds[fi], p->o.mode, 0, (int)fp.nk(), nullptr, nullptr, nullptr,
+                                 p->d_pend, p->pend_cap, p->d_ctr, p->s);
+    stack_launches += n;
+  }
+  CK(cudaEventRecord(p->e1, p->s));
+  L += stack_launches;
+  L += launch_resolve(p->d_fds, nf, p->o.mode, p->d_pend, p->d_ctr, p->pend_cap, p->d_cand,
+                      p->d_keys, p->d_idx, p->pend_cap, p->d_ctr, p->s);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(p->h_ctr, p->d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, p->s));
+  CK(cudaStreamSynchronize(p->s));
+  float ms = 0.0f;
+  CK(cudaEventElapsedTime(&ms, p->e0, p->e1));
+  p->stack_ms = ms;
+  p->stack_launches = stack_launches;
+  Counters c = *p->h_ctr;
+  if (c.error & ERR_PENDING_OVERFLOW) {
+    *h_count = -1;
+    p->launches = L;
+    return fail(ST_ERR_OVERFLOW,
+                "%llu above-threshold points exceed pending_capacity %lld; raise it in st_opts",
+                (unsigned long long)c.n_pending, (long long)p->pend_cap);
+  }
+  int64_t n = (int64_t)c.n_cand;
+  int64_t sn = pow2_at_least(std::max<int64_t>(n, 1));
+  L += launch_pad_keys(p->d_keys, p->d_idx, sn, p->d_ctr, p->s);
+  L += launch_sort_gather(p->d_keys, p->d_idx, sn, p->d_ctr, p->d_cand, d_out, capacity, p->s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(p->s));
+  p->launches = L;
+  p->has_search = true;
+  *h_count = n;
+  if (n > capacity)
+    return fail(ST_ERR_OVERFLOW, "%lld candidates exceed capacity %lld", (long long)n,
+                (long long)capacity);
+  return ST_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t st_version(void) { return ST_VERSION_MAJOR * 100 + ST_VERSION_MINOR; }
+
+const char* st_last_error(void) { return g_err.c_str(); }
+
+st_status st_plan(const st_field* fields, int32_t n_fields, const st_opts* opts,
+                  void* cuda_stream, st_plan_t** out) {
+  if (!out) return fail(ST_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!fields || n_fields <= 0 || n_fields > 255)
+    return fail(ST_ERR_INVALID, "n_fields must be in [1, 255] and fields non-NULL");
+  if (!opts) return fail(ST_ERR_INVALID, "opts is NULL");
+  if (opts->storage < ST_F32 || opts->storage > ST_BF16)
+    return fail(ST_ERR_INVALID, "storage must be ST_F32, ST_F16 or ST_BF16");
+  if (opts->mode != ST_NEAREST && opts->mode != ST_BILINEAR)
+    return fail(ST_ERR_INVALID, "mode must be ST_NEAREST or ST_BILINEAR");
+  if (!std::isfinite(opts->cr_clip) || opts->cr_clip < 0.0f)
+    return fail(ST_ERR_INVALID, "cr_clip must be finite and >= 0");
+  if (opts->pending_capacity < 0 || opts->pending_capacity > (1ll << 31))
+    return fail(ST_ERR_INVALID, "pending_capacity must be in [0, 2^31]");
+  for (int i = 0; i < n_fields; ++i) {
+    st_status st = validate_field(fields[i], i);
+    if (st != ST_OK) return st;
+  }
+  st_plan_t* p = new (std::nothrow) st_plan_s();
+  if (!p) return fail(ST_ERR_OOM, "host allocation failed");
+  p->o = *opts;
+  p->s = (cudaStream_t)cuda_stream;
+  st_status st = ST_OK;
+  auto guard = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && st == ST_OK)
+      st = fail(e == cudaErrorMemoryAllocation ? ST_ERR_OOM : ST_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+    return e == cudaSuccess;
+  };
+  guard(cudaGetDevice(&p->device), "cudaGetDevice");
+  p->F.resize(n_fields);
+  int maxN = 0;
+  for (int i = 0; i < n_fields && st == ST_OK; ++i) {
+    FieldPlan& fp = p->F[i];
+    fp.f = fields[i];
+    const st_field& f = fp.f;
+    maxN = std::max(maxN, f.n_frames);
+    fp.nmin = f.min_coverage > 0 ? f.min_coverage : (f.n_frames + 1) / 2;
+    guard(cudaMalloc(&fp.d_t, sizeof(double) * f.n_frames), "cudaMalloc(times)");
+    guard(cudaMalloc(&fp.d_sx, sizeof(int32_t) * f.n_frames * (size_t)f.nvx), "cudaMalloc(sx)");
+    guard(cudaMalloc(&fp.d_sy, sizeof(int32_t) * f.n_frames * (size_t)f.nvy), "cudaMalloc(sy)");
+    guard(cudaMalloc(&fp.d_fx, sizeof(float) * f.n_frames * (size_t)f.nvx), "cudaMalloc(fx)");
+    guard(cudaMalloc(&fp.d_fy, sizeof(float) * f.n_frames * (size_t)f.nvy), "cudaMalloc(fy)");
+    // threshold and 1/sqrt tables, FP64 formulas rounded once to FP32
+    std::vector<float> thr(f.n_frames + 1), rsq(f.n_frames + 1);
+    for (int n = 0; n <= f.n_frames; ++n) {
+      thr[n] = (float)((double)f.snr_threshold * std::sqrt((double)n));
+      rsq[n] = n > 0 ? (float)(1.0 / std::sqrt((double)n)) : 0.0f;
+    }
+    if (guard(cudaMalloc(&fp.d_thr, sizeof(float) * (f.n_frames + 1)), "cudaMalloc(thr)"))
+      guard(cudaMemcpy(fp.d_thr, thr.data(), sizeof(float) * thr.size(), cudaMemcpyHostToDevice),
+            "cudaMemcpy(thr)");
+    if (guard(cudaMalloc(&fp.d_rsq, sizeof(float) * (f.n_frames + 1)), "cudaMalloc(rsq)"))
+      guard(cudaMemcpy(fp.d_rsq, rsq.data(), sizeof(float) * rsq.size(), cudaMemcpyHostToDevice),
+            "cudaMemcpy(rsq)");
+    if (opts->normalize || opts->storage != ST_F32)
+      guard(cudaMalloc(&fp.d_cube, store_bytes(opts->storage) * (size_t)f.n_frames * fp.P()),
+            "cudaMalloc(cube)");
+  }
+  if (st == ST_OK) {
+    p->pend_cap = opts->pending_capacity > 0 ? opts->pending_capacity : (4ll << 20);
+    p->sort_cap = pow2_at_least(p->pend_cap);
+    guard(cudaMalloc(&p->d_pend, sizeof(Pending) * p->pend_cap), "cudaMalloc(pending)");
+    guard(cudaMalloc(&p->d_cand, sizeof(st_candidate) * p->pend_cap), "cudaMalloc(candidates)");
+    guard(cudaMalloc(&p->d_keys, sizeof(uint64_t) * p->sort_cap), "cudaMalloc(keys)");
+    guard(cudaMalloc(&p->d_idx, sizeof(uint32_t) * p->sort_cap), "cudaMalloc(idx)");
+    guard(cudaMalloc(&p->d_ctr, sizeof(Counters)), "cudaMalloc(counters)");
+    guard(cudaMallocHost(&p->h_ctr, sizeof(Counters)), "cudaMallocHost(counters)");
+    guard(cudaMalloc(&p->d_fds, sizeof(FieldDev) * n_fields), "cudaMalloc(fields)");
+    guard(cudaMalloc(&p->d_sky, sizeof(double) * sky_partial_doubles(maxN)), "cudaMalloc(sky)");
+    guard(cudaEventCreate(&p->e0), "cudaEventCreate");
+    guard(cudaEventCreate(&p->e1), "cudaEventCreate");
+  }
+  if (st != ST_OK) {
+    free_plan(p);
+    return st;
+  }
+  *out = p;
+  return ST_OK;
+}
+
+void st_free(st_plan_t* plan) { free_plan(plan); }
+
+st_status st_stack_search(st_plan_t* p, const float* const* d_frames, const double* const* h_times,
+                          st_candidate* d_out, int64_t capacity, int64_t* h_count) {
+  if (!p) return fail(ST_ERR_INVALID, "plan is NULL");
+  return device_search(p, d_frames, h_times, d_out, capacity, h_count);
+}
+
+st_status st_stack_search_host(st_plan_t* p, const float* const* h_frames,
+                               const double* const* h_times, st_candidate* h_out,
+                               int64_t capacity, int64_t* h_count) {
+  if (!p) return fail(ST_ERR_INVALID, "plan is NULL");
+  if (!h_frames || !h_times || !h_count) return fail(ST_ERR_INVALID, "NULL argument");
+  if (capacity < 0 || (capacity > 0 && !h_out))
+    return fail(ST_ERR_INVALID, "capacity must be >= 0 and h_out non-NULL when capacity > 0");
+  int nf = (int)p->F.size();
+  std::vector<const float*> dptr(nf);
+  for (int fi = 0; fi < nf; ++fi) {
+    FieldPlan& fp = p->F[fi];
+    if (!h_frames[fi]) return fail(ST_ERR_INVALID, "field %d: frames are NULL", fi);
+    size_t bytes = sizeof(float) * (size_t)fp.f.n_frames * fp.P();
+    if (!fp.d_frames_copy) CK(cudaMalloc(&fp.d_frames_copy, bytes));
+    CK(cudaMemcpyAsync(fp.d_frames_copy, h_frames[fi], bytes, cudaMemcpyHostToDevice, p->s));
+    dptr[fi] = fp.d_frames_copy;
+  }
+  if (capacity > p->hout_cap) {
+    cudaFree(p->d_hout);
+    p->d_hout = nullptr;
+    p->hout_cap = 0;
+    CK(cudaMalloc(&p->d_hout, sizeof(st_candidate) * capacity));
+    p->hout_cap = capacity;
+  }
+  st_status st = device_search(p, dptr.data(), h_times, p->d_hout, capacity, h_count);
+  if (st != ST_OK && st != ST_ERR_OVERFLOW) return st;
+  int64_t n = std::min<int64_t>(*h_count < 0 ? 0 : *h_count, capacity);
+  if (n > 0) {
+    CK(cudaMemcpyAsync(h_out, p->d_hout, sizeof(st_candidate) * n, cudaMemcpyDeviceToHost, p->s));
+    CK(cudaStreamSynchronize(p->s));
+  }
+  return st;
+}
+
+st_status st_shift_tables(st_plan_t* p, int32_t field, const double* h_times, int32_t* h_sx,
+                          int32_t* h_sy, float* h_fx, float* h_fy) {
+  if (!p) return fail(ST_ERR_INVALID, "plan is NULL");
+  if (field < 0 || field >= (int)p->F.size()) return fail(ST_ERR_INVALID, "field out of range");
+  if (!h_sx || !h_sy) return fail(ST_ERR_INVALID, "NULL table pointer");
+  FieldPlan& fp = p->F[field];
+  const st_field& f = fp.f;
+  st_status st = check_times(h_times, f.n_frames, f, field);
+  if (st != ST_OK) return st;
+  CK(cudaMemcpyAsync(fp.d_t, h_times, sizeof(double) * f.n_frames, cudaMemcpyHostToDevice, p->s));
+  launch_shift_tables(fp.d_t, f.n_frames, f.t_ref, f.vx0, f.dvx, f.nvx, f.vy0, f.dvy, f.nvy,
+                      p->o.mode, fp.d_sx, fp.d_sy, fp.d_fx, fp.d_fy, p->s);
+  CK(cudaGetLastError());
+  size_t nx = (size_t)f.n_frames * f.nvx, ny = (size_t)f.n_frames * f.nvy;
+  CK(cudaMemcpyAsync(h_sx, fp.d_sx, sizeof(int32_t) * nx, cudaMemcpyDeviceToHost, p->s));
+  CK(cudaMemcpyAsync(h_sy, fp.d_sy, sizeof(int32_t) * ny, cudaMemcpyDeviceToHost, p->s));
+  if (h_fx) CK(cudaMemcpyAsync(h_fx, fp.d_fx, sizeof(float) * nx, cudaMemcpyDeviceToHost, p->s));
+  if (h_fy) CK(cudaMemcpyAsync(h_fy, fp.d_fy, sizeof(float) * ny, cudaMemcpyDeviceToHost, p->s));
+  CK(cudaStreamSynchronize(p->s));
+  return ST_OK;
+}
+
+st_status st_normalize(st_plan_t* p, int32_t field, const float* d_frames, void* d_cube,
+                       double* h_mu, double* h_sigma) {
+  if (!p) return fail(ST_ERR_INVALID, "plan is NULL");
+  if (field < 0 || field >= (int)p->F.size()) return fail(ST_ERR_INVALID, "field out of range");
+  if (!d_frames || !d_cube) return fail(ST_ERR_INVALID, "NULL frames or cube");
+  FieldPlan& fp = p->F[field];
+  const st_field& f = fp.f;
+  double* d_ms = nullptr;
+  CK(cudaMalloc(&d_ms, sizeof(double) * 2 * f.n_frames));
+  launch_normalize(d_frames, f.n_frames, fp.P(), 1, p->o.cr_clip, p->o.storage, d_cube, d_ms,
+                   d_ms + f.n_frames, p->d_sky, p->s);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && h_mu)
+    e = cudaMemcpyAsync(h_mu, d_ms, sizeof(double) * f.n_frames, cudaMemcpyDeviceToHost, p->s);
+  if (e == cudaSuccess && h_sigma)
+    e = cudaMemcpyAsync(h_sigma, d_ms + f.n_frames, sizeof(double) * f.n_frames,
+                        cudaMemcpyDeviceToHost, p->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->s);
+  cudaFree(d_ms);
+  if (e != cudaSuccess) return fail(ST_ERR_CUDA, "st_normalize: %s", cudaGetErrorString(e));
+  return ST_OK;
+}
+
+st_status st_dump_stack(st_plan_t* p, int32_t field, const float* d_frames, const double* h_times,
+                        const int32_t* h_k, int32_t n_k, float* d_S, int32_t* d_ncov) {
+  if (!p) return fail(ST_ERR_INVALID, "plan is NULL");
+  if (field < 0 || field >= (int)p->F.size()) return fail(ST_ERR_INVALID, "field out of range");
+  if (!d_frames || !h_times || !h_k || n_k <= 0 || !d_S)
+    return fail(ST_ERR_INVALID, "NULL argument or n_k <= 0");
+  FieldPlan& fp = p->F[field];
+  for (int q = 0; q < n_k; ++q)
+    if (h_k[q] < 0 || h_k[q] >= fp.nk()) return fail(ST_ERR_INVALID, "velocity index out of range");
+  int64_t L = 0;
+  st_status st = prepare_field(p, field, d_frames, h_times, &L);
+  if (st != ST_OK) return st;
+  int32_t* d_k = nullptr;
+  CK(cudaMalloc(&d_k, sizeof(int32_t) * n_k));
+  cudaError_t e = cudaMemcpyAsync(d_k, h_k, sizeof(int32_t) * n_k, cudaMemcpyHostToDevice, p->s);
+  FieldDev fd = field_dev(fp, d_frames, field, p->o.storage);
+  if (e == cudaSuccess) {
+    launch_stack_generic(fd, p->o.mode, 0, n_k, d_k, d_S, d_ncov, p->d_pend, p->pend_cap, p->d_ctr,
+                         p->s);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->s);
+  cudaFree(d_k);
+  if (e != cudaSuccess) return fail(ST_ERR_CUDA, "st_dump_stack: %s", cudaGetErrorString(e));
+  return ST_OK;
+}
+
+int64_t st_last_launch_count(const st_plan_t* p) { return p ? p->launches : 0; }
+
+st_status st_last_stack_kernel_time(const st_plan_t* p, double* ms, int64_t* launches) {
+  if (!p || !ms || !launches) return fail(ST_ERR_INVALID, "NULL argument");
+  *ms = p->stack_ms;
+  *launches = p->stack_launches;
+  return ST_OK;
+}
+
+st_status st_refine(st_plan_t*, const st_candidate*, int64_t, int32_t, int32_t, float, float, float,
+                    st_refined*, float*) {
+  return fail(ST_ERR_UNSUPPORTED, "st_refine: not built yet");
+}
+
+st_status st_refine_eval(st_plan_t*, const float*, const int32_t*, const int32_t*, int64_t, float,
+                         float*, float*, float*) {
+  return fail(ST_ERR_UNSUPPORTED, "st_refine_eval: not built yet");
+}
+
+}  // extern "C"

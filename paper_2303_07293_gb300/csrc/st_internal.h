@@ -1,0 +1,97 @@
+// st_internal.h — internal types of the synthetic-tracking library (device +
+// host).  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/st.h"
+
+namespace st {
+
+// Above-threshold point waiting for the local-maximum test (24 bytes).
+struct Pending {
+  int32_t x, y, k, field;
+  float S;
+  int32_t n_cov;
+};
+
+// Counters shared by the kernels of one search, in device memory.
+struct Counters {
+  unsigned long long n_pending;   // points written (or attempted) to the pending list
+  unsigned long long n_cand;      // candidates after the local-maximum test
+  unsigned int error;             // bit flags, ERR_*
+  unsigned int pad;
+  unsigned long long work_next;   // persistent-kernel work counter
+};
+
+enum : unsigned { ERR_PENDING_OVERFLOW = 1u, ERR_CAND_OVERFLOW = 2u, ERR_TIMEOUT = 4u };
+
+// Everything a kernel needs to read one field.  Plain data, passed by value.
+struct FieldDev {
+  const void* cube;      // storage cube [N][H][W] of `storage` type
+  int32_t storage;       // st_dtype
+  int32_t W, H, N;
+  int32_t nvx, nvy;
+  int32_t nmin;
+  int32_t field;
+  const int32_t* sx;     // [N][nvx] integer shift (nearest: rounded; bilinear: floor)
+  const int32_t* sy;     // [N][nvy]
+  const float* fx;       // [N][nvx] bilinear fraction
+  const float* fy;       // [N][nvy]
+  const float* thr;      // [N+1] thr[n] = (float)(tau*sqrt(n))
+  const float* rsq;      // [N+1] (float)(1/sqrt(n))
+};
+
+// Key of a candidate: (field, k, y, x) packed into 64 bits, increasing in
+// the output order.
+__host__ __device__ inline uint64_t cand_key(int field, int k, int y, int x) {
+  return ((uint64_t)(uint32_t)field << 56) | ((uint64_t)(uint32_t)k << 30) |
+         ((uint64_t)(uint32_t)y << 15) | (uint64_t)(uint32_t)x;
+}
+
+// ---- kernel launchers (each returns the number of kernels it launched) ----
+
+int launch_shift_tables(const double* d_t, int N, double t_ref, double vx0, double dvx,
+                        int nvx, double vy0, double dvy, int nvy, int mode, int32_t* sx,
+                        int32_t* sy, float* fx, float* fy, cudaStream_t s);
+
+// Sky statistics (FP64, deterministic) and normalisation/conversion.
+//   partial: workspace of sky_partial_doubles(N) doubles.
+size_t sky_partial_doubles(int N);
+int launch_normalize(const float* raw, int N, int64_t npix, int normalize, float cr_clip,
+                     int storage, void* cube, double* mu, double* sigma, double* partial,
+                     cudaStream_t s);
+
+// Generic stack kernels over velocity indices [k0, k0+nk): threshold ->
+// pending list; optional dump of S and n_cov for the listed velocities.
+int launch_stack_generic(const FieldDev& fd, int mode, int k0, int nk, const int32_t* dump_k,
+                         float* dump_S, int32_t* dump_C, Pending* pend, int64_t pend_cap,
+                         Counters* ctr, cudaStream_t s);
+
+// Fast nearest-pixel stack kernel (register-window reuse); returns -1 when the
+// field's geometry does not fit the kernel (caller falls back).
+struct FastPlan;
+int fast_plan_size_bytes();
+bool fast_plan_build(const FieldDev& fd, const int32_t* h_sx, const int32_t* h_sy,
+                     FastPlan** out, cudaStream_t s);
+void fast_plan_free(FastPlan* fp);
+int launch_stack_fast(const FieldDev& fd, const FastPlan* fp, int k0, int nk,
+                      const int32_t* dump_k, float* dump_S, int32_t* dump_C, Pending* pend,
+                      int64_t pend_cap, Counters* ctr, cudaStream_t s);
+
+// Local-maximum test of the pending points -> candidate list (unsorted) and keys.
+int launch_resolve(const FieldDev* fds_dev, int n_fields, int mode, const Pending* pend,
+                   const Counters* ctr, int64_t pend_cap, st_candidate* cand,
+                   uint64_t* keys, uint32_t* idx, int64_t cand_cap, Counters* ctr_out,
+                   cudaStream_t s);
+
+// Sorts keys/idx (n_pow2 entries, padded with ~0) and gathers the first
+// `capacity` records into out.
+int launch_sort_gather(uint64_t* keys, uint32_t* idx, int64_t n_pow2, const Counters* ctr,
+                       const st_candidate* cand, st_candidate* out, int64_t capacity,
+                       cudaStream_t s);
+int launch_pad_keys(uint64_t* keys, uint32_t* idx, int64_t n_pow2, const Counters* ctr,
+                    cudaStream_t s);
+
+}  // namespace st

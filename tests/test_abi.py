@@ -1,0 +1,58 @@
+"""The C-ABI library loads and exports every entry point include/st.h
+declares; host-side argument validation (CPU only: no compute call needs a
+GPU here)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(st_[a-z0-9_]+)\s*\(",
+                            src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ["st_plan", "st_stack_search", "st_refine", "st_free", "st_last_error"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2303_07293_gb300 as st
+    L = st.lib()
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+    assert st.version() == 1
+
+
+def test_invalid_arguments_are_rejected_without_gpu_work():
+    import paper_2303_07293_gb300 as st
+    L = st.lib()
+    h = C.c_void_p()
+    opts = st.Opts(0, 0, 0, 0.0, 0, 0, None, 0)
+    bad = st.Field(0, 10, 4, 0.0, 0.0, 1.0, 1, 0.0, 1.0, 1, 5.0, 0)
+    assert L.st_plan(C.byref(bad), 1, C.byref(opts), None, C.byref(h)) == st.ST_ERR_INVALID
+    assert b"width" in L.st_last_error()
+    assert h.value is None
+    bad2 = st.Field(8, 8, 4, 0.0, 0.0, 1.0, 1, 0.0, 1.0, 1, 5.0, 9)
+    assert L.st_plan(C.byref(bad2), 1, C.byref(opts), None, C.byref(h)) == st.ST_ERR_INVALID
+    assert b"min_coverage" in L.st_last_error()
+    good = st.Field(8, 8, 4, 0.0, 0.0, 1.0, 1, 0.0, 1.0, 1, 5.0, 0)
+    bad_opts = st.Opts(7, 0, 0, 0.0, 0, 0, None, 0)
+    assert L.st_plan(C.byref(good), 1, C.byref(bad_opts), None, C.byref(h)) == st.ST_ERR_INVALID
+    assert L.st_plan(C.byref(good), 0, C.byref(opts), None, C.byref(h)) == st.ST_ERR_INVALID
+    assert L.st_stack_search(None, None, None, None, 0, None) == st.ST_ERR_INVALID
+    L.st_free(None)  # NULL-safe
