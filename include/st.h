@@ -186,6 +186,36 @@ st_status st_refine_eval(st_plan_t* plan, const float* d_theta,
                          int64_t n, float fwhm, float* d_J, float* d_snr,
                          float* d_grad);
 
+/* Search of one field that allocates no memory (the paper has no counterpart:
+ * this serves callers that cannot allocate device memory when they search,
+ * such as code inside a CUDA stream capture that must not add allocation
+ * nodes, or processes whose device memory is reserved up front by another
+ * allocator).  Same kernels, definitions and sorted output as st_stack_search
+ * with normalize = 0 and FP32 storage, for one field (field index 0 in the
+ * records).
+ *   field      : the field (limits as st_plan); mode: ST_NEAREST or ST_BILINEAR.
+ *   d_frames   : device FP32 cube [N][H][W], used as given (not normalised).
+ *   h_times    : host FP64 timestamps [N].
+ *   d_out      : device array of `capacity` candidates (caller-owned).
+ *   h_count    : receives the total number of candidates.
+ *   cuda_stream: cudaStream_t on which the work is ordered; the call
+ *                synchronises it to read the count.
+ * Scratch: one 32 MiB device array inside the library, held by every GPU that
+ * loads the library until the process exits.  It holds the shift tables
+ * (16*N*(nvx+nvy) bytes plus small tables) and 64 bytes per above-threshold
+ * slot; a field whose tables leave fewer than 1024 slots is rejected with
+ * ST_ERR_INVALID, and more above-threshold points than slots gives
+ * ST_ERR_OVERFLOW with *h_count = -1.  No call allocates: the first call on
+ * each device (with that device current) looks up the array's device address
+ * and caches it, so make that first call before any stream capture.  Every
+ * call reuses the same array and the previous call's contents stay in it
+ * (counters are cleared on each call); calls that overlap on the GPU, from
+ * several streams or threads at once, race on it and must be serialised by
+ * the caller. */
+st_status st_stack_search_noalloc(const st_field* field, int32_t mode, const float* d_frames,
+                                  const double* h_times, st_candidate* d_out, int64_t capacity,
+                                  int64_t* h_count, void* cuda_stream);
+
 /* Diagnostics used by the tests. */
 
 /* Shift tables of field f for timestamps h_times: h_sx [N][nvx], h_sy [N][nvy]

@@ -241,5 +241,28 @@ class Plan:
         return ms.value, n.value
 
 
+def search_noalloc(field, frames, times, capacity=1 << 16, mode="nearest", stream=None):
+    """st_stack_search_noalloc: one-field search whose scratch lives in a fixed
+    device array inside the library (for callers that cannot allocate device
+    memory).  frames: contiguous CUDA float32 tensor [N][H][W].  Returns
+    (out tensor [capacity, 7] int32, total count, status).  Calls that overlap
+    on the GPU share the array and must be serialised."""
+    import torch
+    L = lib()
+    L.st_stack_search_noalloc.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
+    if not (frames.is_cuda and frames.dtype == torch.float32 and frames.is_contiguous()):
+        raise ValueError("frames must be a contiguous CUDA float32 tensor")
+    f = make_field(field)
+    t = np.ascontiguousarray(times, np.float64)
+    out = torch.empty((max(capacity, 1), 7), dtype=torch.int32, device=frames.device)
+    cnt = C.c_int64()
+    status = L.st_stack_search_noalloc(C.byref(f), MODE[mode], _ptr(frames), _np_ptr(t),
+                                       _ptr(out), capacity, C.byref(cnt), _stream_handle(stream))
+    if status not in (ST_OK, ST_ERR_OVERFLOW) or cnt.value < 0:
+        _check(status)
+    return out, cnt.value, status
+
+
 def version():
     return lib().st_version()

@@ -54,6 +54,10 @@ int64_t pow2_at_least(int64_t n) {
 
 }  // namespace
 
+namespace st {
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace st
+
 struct FieldPlan {
   st_field f{};
   int nmin = 0;

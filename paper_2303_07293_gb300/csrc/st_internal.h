@@ -50,6 +50,9 @@ __host__ __device__ inline uint64_t cand_key(int field, int k, int y, int x) {
          ((uint64_t)(uint32_t)y << 15) | (uint64_t)(uint32_t)x;
 }
 
+// Sets the message returned by st_last_error() on this thread.
+void set_last_error(const char* msg);
+
 // ---- kernel launchers (each returns the number of kernels it launched) ----
 
 int launch_shift_tables(const double* d_t, int N, double t_ref, double vx0, double dvx,
