@@ -90,7 +90,9 @@ typedef struct {
   float cr_clip;             /* with normalize: zero |I| > cr_clip; 0 disables */
   int32_t use_graph;         /* 1: capture the search of all fields into a CUDA
                                 graph on the first call and replay it later */
-  int32_t tile;              /* stack kernel tile variant; -1 = autotune, 0 = plan default */
+  int32_t tile;              /* stack kernel: -1 = autotuned register-window variant,
+                                0 = default, 1 = direct-gather kernel only,
+                                2.. = register-window variant (tile - 2) */
   const char* tune_cache;    /* JSON file for autotuned tiles, or NULL */
   int64_t pending_capacity;  /* above-threshold points held before the local-max
                                 test; 0 selects a default of 4 Mi points */
@@ -245,6 +247,19 @@ int64_t st_last_launch_count(const st_plan_t* plan);
 /* Average device time in milliseconds of the main stack kernel over the last
  * search call (CUDA events on the plan's stream), and its launch count. */
 st_status st_last_stack_kernel_time(const st_plan_t* plan, double* ms, int64_t* launches);
+
+/* Which stack kernel field f used in the last search on this plan:
+ * 1 = register-window kernel, 0 = direct-gather kernel, -1 = no search yet. */
+int32_t st_last_stack_variant(const st_plan_t* plan, int32_t field);
+
+/* FP32 add-rate microbenchmark (the roof of the nearest-shift stack): one
+ * block of 1024 threads per SM, 16 independent add chains per thread, iters
+ * iterations.  variant 0: scalar add.rn.f32; 1: paired add.rn.f32x2;
+ * 2: paired adds interleaved 1:1 with integer adds.  Writes the median adds
+ * per SM clock (from clock64) and the device-wide rate in T adds/s (CUDA
+ * events).  Allocates and frees its own small buffers. */
+st_status st_probe_add_rate(int32_t variant, int32_t iters, double* adds_per_clk_per_sm,
+                            double* tadds_per_s);
 
 #ifdef __cplusplus
 }

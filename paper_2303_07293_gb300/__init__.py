@@ -76,6 +76,9 @@ def lib():
         L.st_last_launch_count.argtypes = [P]
         L.st_last_launch_count.restype = C.c_int64
         L.st_last_stack_kernel_time.argtypes = [P, P, P]
+        L.st_last_stack_variant.argtypes = [P, C.c_int32]
+        L.st_last_stack_variant.restype = C.c_int32
+        L.st_probe_add_rate.argtypes = [C.c_int32, C.c_int32, P, P]
         _lib = L
     return _lib
 
@@ -231,6 +234,11 @@ class Plan:
                                    ks.size, _ptr(S), _ptr(Cv)))
         return S, Cv
 
+    def last_stack_variant(self, field=0):
+        """1 if field used the register-window kernel in the last search, 0 if
+        the direct-gather kernel, -1 before any search."""
+        return lib().st_last_stack_variant(self._h, field)
+
     def last_launch_count(self):
         return lib().st_last_launch_count(self._h)
 
@@ -239,6 +247,14 @@ class Plan:
         n = C.c_int64()
         _check(lib().st_last_stack_kernel_time(self._h, C.byref(ms), C.byref(n)))
         return ms.value, n.value
+
+
+def probe_add_rate(variant=1, iters=20000):
+    """FP32 add-rate microbenchmark: (adds per SM clock, T adds/s)."""
+    a = C.c_double()
+    t = C.c_double()
+    _check(lib().st_probe_add_rate(variant, iters, C.byref(a), C.byref(t)))
+    return a.value, t.value
 
 
 def search_noalloc(field, frames, times, capacity=1 << 16, mode="nearest", stream=None):

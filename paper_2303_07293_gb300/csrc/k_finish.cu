@@ -61,23 +61,32 @@ __global__ void __launch_bounds__(256)
   int lane = threadIdx.x & 31;
   bool have = p < n;
   Pending r{};
-  bool blocks = false;
+  bool q_in = false;
+  float Sq = 0.0f;
+  int Cq = 0;
+  int nmin = 0;
   if (have) {
     r = pend[p];
     const FieldDev& fd = fds[r.field];
+    nmin = fd.nmin;
     const int dxs[8] = {-1, 0, 1, -1, 1, -1, 0, 1};
     const int dys[8] = {-1, -1, -1, 0, 0, 1, 1, 1};
     int qx = r.x + dxs[nb], qy = r.y + dys[nb];
     if (qx >= 0 && qy >= 0 && qx < fd.W && qy < fd.H) {
-      float Sq;
-      int Cq;
       stack_any<MODE>(fd, qx, qy, r.k % fd.nvx, r.k / fd.nvx, Sq, Cq);
-      if (Cq >= fd.nmin) blocks = nb < 4 ? !(r.S > Sq) : !(r.S >= Sq);
+      q_in = true;
     }
+    // a point recorded by position only: its own sum and coverage, same order
+    if (nb == 0 && r.n_cov < 0) stack_any<MODE>(fd, r.x, r.y, r.k % fd.nvx, r.k / fd.nvx, r.S, r.n_cov);
   }
+  const float Sc = __shfl_sync(0xffffffffu, r.S, lane & ~7);
+  const int Cc = __shfl_sync(0xffffffffu, r.n_cov, lane & ~7);
+  bool center_ok = false;
+  if (have) center_ok = Cc >= nmin && Sc >= __ldg(fds[r.field].thr + Cc);
+  const bool blocks = q_in && Cq >= nmin && (nb < 4 ? !(Sc > Sq) : !(Sc >= Sq));
   unsigned bal = __ballot_sync(0xffffffffu, blocks);
   unsigned group = (bal >> (lane & ~7)) & 0xffu;
-  bool is_cand = have && nb == 0 && group == 0u;
+  bool is_cand = center_ok && nb == 0 && group == 0u;
   unsigned m = __ballot_sync(0xffffffffu, is_cand);
   if (m == 0u) return;
   int leader = __ffs(m) - 1;

@@ -1,26 +1,644 @@
-// k_stack_fast.cu — register-window shift-and-stack kernel (placeholder until
-// the tiled kernel lands; the planner falls back to the generic kernel).
+// k_stack_fast.cu — register-window shift-and-stack kernel for sm_103a.
+//
+// Computes the same nearest-pixel stack as the generic kernel (Sec. 1 /
+// Sec. 2.1: every frame shifted by the rounded trial motion v*(t_i - t_ref)
+// and summed in frame order with one FP32 accumulator per output), laid out
+// for the GB300 FP32 pipe:
+//
+// * A block owns a 32 x 32 pixel tile and a velocity tile of 8 x-velocities
+//   (one per warp) times 4 y-velocities (shared by all warps).  Lane l owns
+//   column X0 + l; each thread accumulates the 32 rows of its column for its
+//   warp's x-velocity and the 4 y-velocities: 128 FP32 accumulators.
+// * Per frame, one elected thread issues a TMA tile load of the block's
+//   footprint (40 x 35 FP32, zero-filled outside the frame) into a ring of
+//   shared-memory stages guarded by mbarriers (full: bytes landed; empty: all
+//   warps done).  Every wait is bounded.
+// * A warp's x-shift is only an address: lane l reads column l + o_w, so the
+//   32 lanes read 32 consecutive words (no bank conflicts, any alignment).
+// * Each thread loads a 35-row window of its column and reuses every value
+//   for the 4 y-velocities: y-velocity j adds window[r + c_j] to row r.  The
+//   row offsets c_j form a monotone staircase with steps of 0 or 1 (15
+//   patterns); the pattern is the same for the whole block in a frame and
+//   comes from the kernel parameters, so one uniform switch per frame picks a
+//   straight-line body.  Even offsets use paired adds (add.f32x2) on row
+//   pairs, odd offsets scalar adds; both cost the same FMA-pipe cycles.
+// * After the last frame, outputs are compared with the block's lowest
+//   possible threshold; the rare survivors get their exact coverage and go
+//   to the warp-aggregated pending list for the local-maximum test.
+//
+// The sums are the same FP32 additions in the same order as the generic
+// kernel (out-of-frame samples add +0.0 from the TMA zero fill, which leaves
+// any sum unchanged), so the two kernels agree bit for bit.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstring>
+#include <new>
+#include <utility>
+
 #include "st_internal.h"
+#include "st_pending.cuh"
+#include "st_tma.cuh"
 
 namespace st {
 
+namespace {
+
+constexpr int kXV = 8;           // x-velocities per block, one per warp (within a row group)
+constexpr int kMB = 4;           // y-velocities per block (staircase group)
+constexpr int kTX = 32, kTY = 32;  // pixel tile
+constexpr int kBoxW = 40;        // shared row pitch and TMA box width (floats)
+constexpr int kBoxH = kTY + 3;   // tile rows + largest staircase offset
+constexpr int kOColMax = kBoxW - kTX;  // largest column offset of a warp
+constexpr int kSuper = 4;        // pixel tiles per super-tile side (L2 locality)
+constexpr uint32_t kMaxPolls = 1u << 22;
+constexpr int kParamBytes = 28672;  // staircase pattern ids carried in the kernel parameters
+constexpr int kPatterns = 15;
+
+struct FastArgs {
+  int W, H, N, nvx, nvy, nA, nB, stage_floats;
+  int B0, G;        // this launch covers y-velocity groups B0 .. B0+G-1
+  int64_t n_items;  // work items of this launch
+  int tiles_x, tiles_y, super_x, super_y;
+  int nmin, field;
+  const int4* xt;   // [N][nA]: box x offset, packed 4-bit column offsets, min shift, max shift
+  const int4* yt;   // [N][nB]: min shift, max shift, pattern id, 0
+  const int* xmin;  // [nA] min over frames of the min shift
+  const int* xmax;  // [nA] max over frames of the max shift
+  const int* ymin;  // [nB]
+  const int* ymax;  // [nB]
+  const int32_t* sx;
+  const int32_t* sy;
+  const float* thr;
+  Pending* pend;
+  int64_t cap;
+  Counters* ctr;
+  float* dump_S;    // optional [nvx*nvy][H][W] (tests)
+  int32_t* dump_C;
+  // [G][N] staircase pattern ids.  Parameter-space loads are uniform, so the
+  // per-frame switch is a uniform branch.
+  unsigned char pat[kParamBytes];
+};
+
+// Pattern id -> row offsets of the 4 y-velocities (min offset 0).
+// ids 0..7: non-decreasing, steps (id&1, id>>1&1, id>>2&1);
+// ids 8..14: non-increasing, steps of t = id - 7 read from the other end.
+__host__ __device__ constexpr int pat_off(int id, int j) {
+  if (id < 8) {
+    int s1 = id & 1, s2 = (id >> 1) & 1, s3 = (id >> 2) & 1;
+    return j == 0 ? 0 : j == 1 ? s1 : j == 2 ? s1 + s2 : s1 + s2 + s3;
+  }
+  int t = id - 7;
+  int t1 = t & 1, t2 = (t >> 1) & 1, t3 = (t >> 2) & 1;
+  return j == 0 ? t1 + t2 + t3 : j == 1 ? t2 + t3 : j == 2 ? t3 : 0;
+}
+
+__device__ int pattern_of(const int (&c)[kMB]) {
+  for (int id = 0; id < kPatterns; ++id) {
+    bool m = true;
+    for (int j = 0; j < kMB; ++j) m = m && (pat_off(id, j) == c[j]);
+    if (m) return id;
+  }
+  return 255;
+}
+
+__global__ void k_fast_tables(const int32_t* __restrict__ sx, const int32_t* __restrict__ sy,
+                              int N, int nvx, int nvy, int nA, int nB, int4* __restrict__ xt,
+                              int4* __restrict__ yt, int* xmin, int* xmax, int* ymin, int* ymax,
+                              int* maxes, unsigned char* __restrict__ pat) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t nX = (int64_t)N * nA, nY = (int64_t)N * nB;
+  if (idx < nX) {
+    int i = (int)(idx / nA), A = (int)(idx % nA);
+    int s[kXV], mn = INT_MAX, mx = INT_MIN;
+#pragma unroll
+    for (int j = 0; j < kXV; ++j) {
+      int a = min(A * kXV + j, nvx - 1);
+      s[j] = sx[(int64_t)i * nvx + a];
+      mn = min(mn, s[j]);
+      mx = max(mx, s[j]);
+    }
+    int xs = mn & ~3;  // 16-byte aligned box origin (floor to a multiple of 4)
+    uint32_t packed = 0;
+    int om = 0;
+#pragma unroll
+    for (int j = 0; j < kXV; ++j) {
+      int o = s[j] - xs;
+      om = max(om, o);
+      packed |= (uint32_t)min(o, 15) << (4 * j);
+    }
+    xt[idx] = make_int4(xs, (int)packed, mn, mx);
+    atomicMax(&maxes[0], om);
+    atomicMin(&xmin[A], mn);
+    atomicMax(&xmax[A], mx);
+  } else if (idx < nX + nY) {
+    int64_t j2 = idx - nX;
+    int i = (int)(j2 / nB), B = (int)(j2 % nB);
+    int s[kMB], mn = INT_MAX, mx = INT_MIN;
+#pragma unroll
+    for (int j = 0; j < kMB; ++j) {
+      int b = min(B * kMB + j, nvy - 1);
+      s[j] = sy[(int64_t)i * nvy + b];
+      mn = min(mn, s[j]);
+      mx = max(mx, s[j]);
+    }
+    int c[kMB];
+#pragma unroll
+    for (int j = 0; j < kMB; ++j) c[j] = s[j] - mn;
+    int id = pattern_of(c);
+    yt[j2] = make_int4(mn, mx, id, 0);
+    pat[j2] = (unsigned char)id;
+    atomicMax(&maxes[1], id);
+    atomicMin(&ymin[B], mn);
+    atomicMax(&ymax[B], mx);
+  }
+}
+
+// acc[j][r] += window[r + C] for the KY rows of a thread, as KY/2 row pairs.
+template <int KY, int C, int M>
+__device__ __forceinline__ void add_rows(float2 (&acc)[KY / 2], const float (&w)[KY + 3]) {
+  if constexpr ((C & 1) == 0) {
+    acc[M] = __fadd2_rn(acc[M], make_float2(w[2 * M + C], w[2 * M + C + 1]));
+  } else {
+    acc[M].x = __fadd_rn(acc[M].x, w[2 * M + C]);
+    acc[M].y = __fadd_rn(acc[M].y, w[2 * M + C + 1]);
+  }
+}
+
+template <int KY, int C, int... M>
+__device__ __forceinline__ void add_column(float2 (&acc)[KY / 2], const float (&w)[KY + 3],
+                                           std::integer_sequence<int, M...>) {
+  (add_rows<KY, C, M>(acc, w), ...);
+}
+
+template <int KY, int ID>
+__device__ __forceinline__ void add_pattern(float2 (&acc)[kMB][KY / 2], const float (&w)[KY + 3]) {
+  add_column<KY, pat_off(ID, 0)>(acc[0], w, std::make_integer_sequence<int, KY / 2>{});
+  add_column<KY, pat_off(ID, 1)>(acc[1], w, std::make_integer_sequence<int, KY / 2>{});
+  add_column<KY, pat_off(ID, 2)>(acc[2], w, std::make_integer_sequence<int, KY / 2>{});
+  add_column<KY, pat_off(ID, 3)>(acc[3], w, std::make_integer_sequence<int, KY / 2>{});
+}
+
+__device__ int exact_coverage(const FastArgs& p, int x, int y, int av, int bv) {
+  int c = 0;
+  for (int i = 0; i < p.N; ++i) {
+    int u = x + __ldg(p.sx + (int64_t)i * p.nvx + av);
+    int w = y + __ldg(p.sy + (int64_t)i * p.nvy + bv);
+    c += (u >= 0 && u < p.W && w >= 0 && w < p.H);
+  }
+  return c;
+}
+
+// Work item -> tile and velocity tile.  Items are ordered (super-tile,
+// velocity tile, sub-tile) with the sub-tile fastest, so consecutive items
+// (which neighbouring CTAs run at the same time) share most of their frame
+// footprints in L2.
+struct Item {
+  int X0, Y0, A, g, B;
+};
+__device__ __forceinline__ Item decode_item(const FastArgs& p, int64_t L) {
+  const int nVT = p.nA * p.G;
+  const int sub = (int)(L % (kSuper * kSuper));
+  const int64_t rest = L / (kSuper * kSuper);
+  const int vt = (int)(rest % nVT);
+  const int stile = (int)(rest / nVT);
+  Item it;
+  it.X0 = ((stile % p.super_x) * kSuper + sub % kSuper) * kTX;
+  it.Y0 = ((stile / p.super_x) * kSuper + sub / kSuper) * kTY;
+  it.A = vt % p.nA;
+  it.g = vt / p.nA;
+  it.B = p.B0 + it.g;
+  return it;
+}
+
+// Persistent kernel: every CTA walks the items blockIdx.x, blockIdx.x +
+// gridDim.x, ...  A ring of S stages of F frames each runs continuously
+// across items: the producer (thread 0) keeps refilling free stages, so the
+// next item's first frames load while the current item finishes and runs its
+// epilogue.  Barrier handshakes are per stage (F frames); the ring and item
+// bookkeeping is incremental 32-bit arithmetic.
+// KY rows per thread; WY row groups of 8 warps (8*WY warps per CTA).
+template <int KY, int WY, int S, int F, bool DUMP>
+__global__ void __launch_bounds__(32 * kXV * WY, 1)
+    k_stack_fast(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ FastArgs p) {
+  static_assert(KY * WY == kTY, "row groups must cover the tile");
+  constexpr int kCW = kXV * WY;  // warps per CTA, all consumers
+  constexpr int kOut = kMB * KY;  // outputs per thread per item
+  extern __shared__ __align__(128) float smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[S];
+  __shared__ __align__(8) uint64_t empty_bar[S];
+
+  float* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u) / sizeof(float);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int xw = warp % kXV, rg = warp / kXV;
+  const uint32_t box_bytes = (uint32_t)kBoxH * kBoxW * sizeof(float);
+  const int box_floats = p.stage_floats;  // one frame's box, 128-byte aligned
+  const int N = p.N;
+  const int G = (int)gridDim.x;
+  const int my_items = (int)blockIdx.x < p.n_items ? (int)((p.n_items - blockIdx.x + G - 1) / G) : 0;
+  const int q_total = my_items * N;           // (item, frame) pairs of this CTA, in order
+  const int n_stages = (q_total + F - 1) / F;  // stages of this CTA, in order
+
+  if (tid == 0) {
+    tma_prefetch_desc(&tmap);
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], kCW);
+    }
+    mbar_init_fence();
+  }
+  __syncthreads();
+
+  // producer state (thread 0): next stage to issue and the pair it starts at
+  int p_seq = 0, p_slot = 0;
+  int p_item = 0, p_frame = 0;
+  Item p_it = decode_item(p, blockIdx.x);
+
+  bool ok = true;
+  int c_seq = 0, c_slot = 0, c_sub = 0;  // consumer position in the ring
+  uint32_t c_ph = 0;
+  int item = 0, f = 0;
+  Item it = decode_item(p, blockIdx.x);
+  float2 acc[kMB][KY / 2];
+#pragma unroll
+  for (int j = 0; j < kMB; ++j)
+#pragma unroll
+    for (int m = 0; m < KY / 2; ++m) acc[j][m] = make_float2(0.0f, 0.0f);
+
+  for (int q = 0; q < q_total; ++q) {
+    if (c_sub == 0) {
+      // producer: refill every free stage without waiting; wait (bounded)
+      // only when the stage about to be consumed is not issued yet
+      if (tid == 0) {
+        while (p_seq < n_stages) {
+          if (p_seq >= S) {
+            const uint32_t par = (uint32_t)(p_seq / S - 1) & 1u;
+            const bool free_ = p_seq <= c_seq ? mbar_wait(&empty_bar[p_slot], par, kMaxPolls)
+                                              : mbar_test(&empty_bar[p_slot], par);
+            if (!free_) {
+              if (p_seq <= c_seq) atomicOr(&p.ctr->error, ERR_TIMEOUT);
+              break;
+            }
+          }
+          const int nbox = min(F, q_total - p_seq * F);
+          mbar_arrive_expect_tx(&full_bar[p_slot], box_bytes * (uint32_t)nbox);
+          for (int b = 0; b < nbox; ++b) {
+            const int4 xe = __ldg(p.xt + (int64_t)p_frame * p.nA + p_it.A);
+            const int4 ye = __ldg(p.yt + (int64_t)p_frame * p.nB + p_it.B);
+            tma_load_3d(smem + (size_t)(p_slot * F + b) * box_floats, &tmap, p_it.X0 + xe.x,
+                        p_it.Y0 + ye.x, p_frame, &full_bar[p_slot]);
+            if (++p_frame == N) {
+              p_frame = 0;
+              ++p_item;
+              if (p_item < my_items) p_it = decode_item(p, blockIdx.x + (int64_t)p_item * G);
+            }
+          }
+          ++p_seq;
+          if (++p_slot == S) p_slot = 0;
+        }
+      }
+      const bool got = mbar_wait(&full_bar[c_slot], c_ph, kMaxPolls);
+      if (!__all_sync(0xffffffffu, got)) {  // bounded wait ran out: leave (warp-uniform)
+        if (lane == 0) atomicOr(&p.ctr->error, ERR_TIMEOUT);
+        ok = false;
+        break;
+      }
+    }
+    const int ocol = ((uint32_t)__ldg(&p.xt[(int64_t)f * p.nA + it.A].y) >> (4 * xw)) & 15u;
+    const int id = p.pat[it.g * N + f];
+    const float* col =
+        smem + (size_t)(c_slot * F + c_sub) * box_floats + rg * KY * kBoxW + lane + ocol;
+    float w[KY + 3];
+#pragma unroll
+    for (int r = 0; r < KY + 3; ++r) w[r] = col[r * kBoxW];
+    if (++c_sub == F || q + 1 == q_total) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty_bar[c_slot]);
+      c_sub = 0;
+      ++c_seq;
+      if (++c_slot == S) {
+        c_slot = 0;
+        c_ph ^= 1u;
+      }
+    }
+    switch (id) {
+      case 0: add_pattern<KY, 0>(acc, w); break;
+      case 1: add_pattern<KY, 1>(acc, w); break;
+      case 2: add_pattern<KY, 2>(acc, w); break;
+      case 3: add_pattern<KY, 3>(acc, w); break;
+      case 4: add_pattern<KY, 4>(acc, w); break;
+      case 5: add_pattern<KY, 5>(acc, w); break;
+      case 6: add_pattern<KY, 6>(acc, w); break;
+      case 7: add_pattern<KY, 7>(acc, w); break;
+      case 8: add_pattern<KY, 8>(acc, w); break;
+      case 9: add_pattern<KY, 9>(acc, w); break;
+      case 10: add_pattern<KY, 10>(acc, w); break;
+      case 11: add_pattern<KY, 11>(acc, w); break;
+      case 12: add_pattern<KY, 12>(acc, w); break;
+      case 13: add_pattern<KY, 13>(acc, w); break;
+      default: add_pattern<KY, 14>(acc, w); break;
+    }
+    if (++f < N) continue;
+
+    // ---- epilogue of the item
+    f = 0;
+    int n_full;
+    const bool interior =
+        it.X0 + __ldg(p.xmin + it.A) >= 0 && it.X0 + kTX - 1 + __ldg(p.xmax + it.A) < p.W &&
+        it.Y0 + __ldg(p.ymin + it.B) >= 0 && it.Y0 + kTY - 1 + __ldg(p.ymax + it.B) < p.H;
+    if (interior) {
+      n_full = N;
+    } else {
+      // per warp (no CTA barrier in the loop): frames whose footprint is inside
+      n_full = 0;
+      for (int i0 = 0; i0 < N; i0 += 32) {
+        const int i = i0 + lane;
+        bool in = false;
+        if (i < N) {
+          const int4 xe = __ldg(p.xt + (int64_t)i * p.nA + it.A);
+          const int4 ye = __ldg(p.yt + (int64_t)i * p.nB + it.B);
+          in = it.X0 + xe.z >= 0 && it.X0 + kTX - 1 + xe.w < p.W && it.Y0 + ye.x >= 0 &&
+               it.Y0 + kTY - 1 + ye.y < p.H;
+        }
+        n_full += __popc(__ballot_sync(0xffffffffu, in));
+      }
+    }
+    const int x = it.X0 + lane;
+    const int av = it.A * kXV + xw;
+    const int y0 = it.Y0 + rg * KY;
+    if constexpr (DUMP) {
+#pragma unroll
+      for (int j = 0; j < kMB; ++j)
+#pragma unroll
+        for (int m = 0; m < KY / 2; ++m)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int bv = it.B * kMB + j, y = y0 + 2 * m + h;
+            if (x < p.W && y < p.H && av < p.nvx && bv < p.nvy) {
+              const int64_t o =
+                  ((int64_t)bv * p.nvx + av) * p.W * (int64_t)p.H + (int64_t)y * p.W + x;
+              p.dump_S[o] = h == 0 ? acc[j][m].x : acc[j][m].y;
+              if (p.dump_C) p.dump_C[o] = exact_coverage(p, x, y, av, bv);
+            }
+          }
+    } else {
+      // outputs at or above the block's lowest possible threshold, as a
+      // bitmask; the exact coverage, threshold and local-maximum test of
+      // these rare points happen in the resolver
+      const float thr_lo = __ldg(p.thr + max(n_full, p.nmin));
+      uint32_t mask[kOut / 32];
+#pragma unroll
+      for (int b = 0; b < kOut / 32; ++b) mask[b] = 0u;
+#pragma unroll
+      for (int j = 0; j < kMB; ++j)
+#pragma unroll
+        for (int m = 0; m < KY / 2; ++m) {
+          const int o = j * KY + 2 * m;
+          mask[o / 32] |= (uint32_t)(acc[j][m].x >= thr_lo) << (o % 32);
+          mask[o / 32] |= (uint32_t)(acc[j][m].y >= thr_lo) << (o % 32 + 1);
+        }
+      const bool col_ok = x < p.W && av < p.nvx;
+      for (int b = 0; b < kOut / 32; ++b) {
+        uint32_t mk = col_ok ? mask[b] : 0u;
+        while (__any_sync(0xffffffffu, mk != 0u)) {
+          const bool has = mk != 0u;
+          const int bit = has ? __ffs(mk) - 1 : 0;
+          mk &= has ? mk - 1u : 0u;
+          const int o = b * 32 + bit;
+          const int j = o / KY, y = y0 + o % KY, bv = it.B * kMB + j;
+          const bool valid = has && y < p.H && bv < p.nvy;
+          Pending rec{x, y, bv * p.nvx + av, p.field, 0.0f, -1};
+          push_pending(valid, rec, p.pend, p.cap, p.ctr);
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kMB; ++j)
+#pragma unroll
+      for (int m = 0; m < KY / 2; ++m) acc[j][m] = make_float2(0.0f, 0.0f);
+    if (++item < my_items) it = decode_item(p, blockIdx.x + (int64_t)item * G);
+  }
+  if (tid == 0) {
+    // stages still in flight (only after a timeout): wait for them, bounded
+    int slot = c_slot;
+    uint32_t ph = c_ph;
+    for (int sq = c_seq; sq < p_seq; ++sq) {
+      mbar_wait(&full_bar[slot], ph, kMaxPolls);
+      if (++slot == S) {
+        slot = 0;
+        ph ^= 1u;
+      }
+    }
+  }
+}
+
+// Compiled variants: (rows per thread, row groups, stages), each with and
+// without the stack dump used by the tests.
+struct Variant {
+  void (*fn)(CUtensorMap, FastArgs);
+  void (*dump_fn)(CUtensorMap, FastArgs);
+  int threads, stages;
+  const char* name;
+};
+
+#define ST_VARIANT(KY, WY, S, F)                                                             \
+  {                                                                                          \
+    (void (*)(CUtensorMap, FastArgs))k_stack_fast<KY, WY, S, F, false>,                        \
+        (void (*)(CUtensorMap, FastArgs))k_stack_fast<KY, WY, S, F, true>, 32 * kXV * WY, S * F, \
+        "ky" #KY "_wy" #WY "_s" #S "_f" #F                                                    \
+  }
+const Variant kVariants[] = {ST_VARIANT(32, 1, 6, 4), ST_VARIANT(16, 2, 6, 4), ST_VARIANT(32, 1, 12, 2),
+                             ST_VARIANT(16, 2, 12, 2)};
+#undef ST_VARIANT
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+}  // namespace
+
 struct FastPlan {
-  int unused;
+  CUtensorMap tmap;
+  const void* encoded_for = nullptr;
+  int variant = 0;  // index into kVariants
+  int nA = 0, nB = 0, N = 0;
+  unsigned char* d_pat = nullptr;  // [N][nB] pattern ids
+  unsigned char* h_pat = nullptr;  // pinned copy for the kernel parameters
+  int4* xt = nullptr;
+  int4* yt = nullptr;
+  int* ranges = nullptr;  // xmin[nA], xmax[nA], ymin[nB], ymax[nB], maxes[2]
+  int* h_maxes = nullptr; // pinned
 };
 
 int fast_plan_size_bytes() { return (int)sizeof(FastPlan); }
 
-bool fast_plan_build(const FieldDev&, const int32_t*, const int32_t*, FastPlan** out,
-                     cudaStream_t) {
-  *out = nullptr;
-  return false;
+int fast_num_variants() { return kNumVariants; }
+const char* fast_variant_name(int v) { return v >= 0 && v < kNumVariants ? kVariants[v].name : "?"; }
+void fast_set_variant(FastPlan* fp, int v) {
+  if (fp && v >= 0 && v < kNumVariants) fp->variant = v;
 }
 
-void fast_plan_free(FastPlan* fp) { delete fp; }
+bool fast_eligible(const FieldDev& fd, int mode) {
+  return mode == ST_NEAREST && fd.storage == ST_F32 && fd.W % 4 == 0 && encode_fn() != nullptr &&
+         fd.W >= 8 && fd.H >= 1;
+}
 
-int launch_stack_fast(const FieldDev&, const FastPlan*, int, int, const int32_t*, float*,
-                      int32_t*, Pending*, int64_t, Counters*, cudaStream_t) {
-  return -1;
+bool fast_plan_build(const FieldDev& fd, const int32_t*, const int32_t*, FastPlan** out,
+                     cudaStream_t) {
+  *out = nullptr;
+  FastPlan* fp = new (std::nothrow) FastPlan();
+  if (!fp) return false;
+  fp->nA = (fd.nvx + kXV - 1) / kXV;
+  fp->nB = (fd.nvy + kMB - 1) / kMB;
+  fp->N = fd.N;
+  bool good = cudaMalloc(&fp->xt, sizeof(int4) * (size_t)fd.N * fp->nA) == cudaSuccess &&
+              cudaMalloc(&fp->yt, sizeof(int4) * (size_t)fd.N * fp->nB) == cudaSuccess &&
+              cudaMalloc(&fp->ranges, sizeof(int) * (2 * fp->nA + 2 * fp->nB + 2)) == cudaSuccess &&
+              cudaMallocHost(&fp->h_maxes, sizeof(int) * 2) == cudaSuccess &&
+              cudaMalloc(&fp->d_pat, (size_t)fd.N * fp->nB) == cudaSuccess &&
+              cudaMallocHost(&fp->h_pat, (size_t)fd.N * fp->nB) == cudaSuccess;
+  if (!good) {
+    fast_plan_free(fp);
+    return false;
+  }
+  *out = fp;
+  return true;
+}
+
+void fast_plan_free(FastPlan* fp) {
+  if (!fp) return;
+  cudaFree(fp->xt);
+  cudaFree(fp->yt);
+  cudaFree(fp->ranges);
+  if (fp->h_maxes) cudaFreeHost(fp->h_maxes);
+  cudaFree(fp->d_pat);
+  if (fp->h_pat) cudaFreeHost(fp->h_pat);
+  delete fp;
+}
+
+// Builds the per-frame tile tables and reports whether the field's motion
+// fits the kernel (column offsets <= 8 within 8 x-velocities, staircase row
+// offsets within 4 y-velocities).  Synchronises s.
+int fast_prepare(const FieldDev& fd, FastPlan* fp, cudaStream_t s, bool* fits) {
+  *fits = false;
+  int nA = fp->nA, nB = fp->nB;
+  int* xmin = fp->ranges;
+  int* xmax = xmin + nA;
+  int* ymin = xmax + nA;
+  int* ymax = ymin + nB;
+  int* maxes = ymax + nB;
+  cudaMemsetAsync(xmin, 0x7f, sizeof(int) * nA, s);
+  cudaMemsetAsync(xmax, 0x80, sizeof(int) * nA, s);
+  cudaMemsetAsync(ymin, 0x7f, sizeof(int) * nB, s);
+  cudaMemsetAsync(ymax, 0x80, sizeof(int) * nB, s);
+  cudaMemsetAsync(maxes, 0, sizeof(int) * 2, s);
+  int64_t n = (int64_t)fd.N * (nA + nB);
+  k_fast_tables<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(fd.sx, fd.sy, fd.N, fd.nvx, fd.nvy, nA,
+                                                            nB, fp->xt, fp->yt, xmin, xmax, ymin,
+                                                            ymax, maxes, fp->d_pat);
+  cudaMemcpyAsync(fp->h_maxes, maxes, sizeof(int) * 2, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(fp->h_pat, fp->d_pat, (size_t)fd.N * nB, cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return 1;
+  *fits = fp->h_maxes[0] <= kOColMax && fp->h_maxes[1] < kPatterns && fd.N <= kParamBytes;
+  return 1;
+}
+
+int launch_stack_fast(const FieldDev& fd, const FastPlan* cfp, int k0, int nk,
+                      const int32_t* dump_k, float* dump_S, int32_t* dump_C, Pending* pend,
+                      int64_t pend_cap, Counters* ctr, cudaStream_t s) {
+  FastPlan* fp = const_cast<FastPlan*>(cfp);
+  if (k0 != 0 || nk != fd.nvx * fd.nvy || dump_k) return -1;  // whole grid only
+  if (fp->encoded_for != fd.cube) {
+    cuuint64_t dims[3] = {(cuuint64_t)fd.W, (cuuint64_t)fd.H, (cuuint64_t)fd.N};
+    cuuint64_t strides[2] = {(cuuint64_t)fd.W * 4, (cuuint64_t)fd.W * fd.H * 4};
+    cuuint32_t box[3] = {(cuuint32_t)kBoxW, (cuuint32_t)kBoxH, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = encode_fn()(&fp->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                             const_cast<void*>(fd.cube), dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return -1;
+    fp->encoded_for = fd.cube;
+  }
+  thread_local static FastArgs a;  // large parameter-space block, filled per launch
+  std::memset(&a, 0, sizeof a);
+  a.W = fd.W;
+  a.H = fd.H;
+  a.N = fd.N;
+  a.nvx = fd.nvx;
+  a.nvy = fd.nvy;
+  a.nA = fp->nA;
+  a.nB = fp->nB;
+  int stage_bytes = ((kBoxH * kBoxW * 4) + 127) & ~127;
+  a.stage_floats = stage_bytes / 4;
+  a.tiles_x = (fd.W + kTX - 1) / kTX;
+  a.tiles_y = (fd.H + kTY - 1) / kTY;
+  a.super_x = (a.tiles_x + kSuper - 1) / kSuper;
+  a.super_y = (a.tiles_y + kSuper - 1) / kSuper;
+  a.nmin = fd.nmin;
+  a.field = fd.field;
+  a.xt = fp->xt;
+  a.yt = fp->yt;
+  a.xmin = fp->ranges;
+  a.xmax = fp->ranges + fp->nA;
+  a.ymin = fp->ranges + 2 * fp->nA;
+  a.ymax = fp->ranges + 2 * fp->nA + fp->nB;
+  a.sx = fd.sx;
+  a.sy = fd.sy;
+  a.thr = fd.thr;
+  a.pend = pend;
+  a.cap = pend_cap;
+  a.ctr = ctr;
+  a.dump_S = dump_S;
+  a.dump_C = dump_C;
+  const Variant& var = kVariants[fp->variant];
+  void (*fn)(CUtensorMap, FastArgs) = dump_S ? var.dump_fn : var.fn;
+  size_t smem = (size_t)var.stages * stage_bytes + 128;
+  static bool attr_set[2 * kNumVariants] = {};
+  const int attr_i = 2 * fp->variant + (dump_S ? 1 : 0);
+  if (!attr_set[attr_i]) {
+    cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set[attr_i] = true;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int G = kParamBytes / fd.N < fp->nB ? kParamBytes / fd.N : fp->nB;
+  if (G < 1) return -1;
+  int launches = 0;
+  for (int B0 = 0; B0 < fp->nB; B0 += G) {
+    a.B0 = B0;
+    a.G = fp->nB - B0 < G ? fp->nB - B0 : G;
+    for (int g = 0; g < a.G; ++g)
+      for (int i = 0; i < fd.N; ++i) a.pat[g * fd.N + i] = fp->h_pat[(size_t)i * fp->nB + B0 + g];
+    a.n_items = (int64_t)a.super_x * a.super_y * kSuper * kSuper * a.nA * a.G;
+    const int64_t grid = a.n_items < sms ? a.n_items : sms;  // one persistent CTA per SM
+    void* args[2] = {&fp->tmap, &a};
+    if (cudaLaunchKernel((const void*)fn, dim3((unsigned)grid), dim3(var.threads), args, smem, s) !=
+        cudaSuccess)
+      return -1;
+    ++launches;
+  }
+  return launches;
 }
 
 }  // namespace st

@@ -71,7 +71,7 @@ struct FieldPlan {
   void* d_cube = nullptr;        // normalised / converted storage cube (owned)
   float* d_frames_copy = nullptr; // device copy for the host-buffer entry point
   FastPlan* fast = nullptr;
-  bool fast_checked = false;
+  int last_variant = -1;
   const float* last_frames = nullptr;
   int64_t P() const { return (int64_t)f.width * f.height; }
   int64_t nk() const { return (int64_t)f.nvx * f.nvy; }
@@ -220,12 +220,27 @@ st_status device_search(st_plan_t* p, const float* const* d_frames, const double
   }
   CK(cudaMemcpyAsync(p->d_fds, fds.data(), sizeof(FieldDev) * nf, cudaMemcpyHostToDevice, p->s));
   CK(cudaMemsetAsync(p->d_ctr, 0, sizeof(Counters), p->s));
+  std::vector<char> use_fast(nf, 0);
+  for (int fi = 0; fi < nf; ++fi) {
+    bool fits = false;
+    if (p->F[fi].fast) {
+      L += fast_prepare(fds[fi], p->F[fi].fast, p->s, &fits);
+      CK(cudaGetLastError());
+    }
+    use_fast[fi] = fits;
+  }
   CK(cudaEventRecord(p->e0, p->s));
   int64_t stack_launches = 0;
   for (int fi = 0; fi < nf; ++fi) {
     FieldPlan& fp = p->F[fi];
-    int n = launch_stack_generic(fds[fi], p->o.mode, 0, (int)fp.nk(), nullptr, nullptr, nullptr,
-                                 p->d_pend, p->pend_cap, p->d_ctr, p->s);
+    int n = -1;
+    if (use_fast[fi])
+      n = launch_stack_fast(fds[fi], fp.fast, 0, (int)fp.nk(), nullptr, nullptr, nullptr,
+                            p->d_pend, p->pend_cap, p->d_ctr, p->s);
+    fp.last_variant = n >= 0 ? 1 : 0;
+    if (n < 0)
+      n = launch_stack_generic(fds[fi], p->o.mode, 0, (int)fp.nk(), nullptr, nullptr, nullptr,
+                               p->d_pend, p->pend_cap, p->d_ctr, p->s);
     stack_launches += n;
   }
   CK(cudaEventRecord(p->e1, p->s));
@@ -283,6 +298,9 @@ st_status st_plan(const st_field* fields, int32_t n_fields, const st_opts* opts,
     return fail(ST_ERR_INVALID, "mode must be ST_NEAREST or ST_BILINEAR");
   if (!std::isfinite(opts->cr_clip) || opts->cr_clip < 0.0f)
     return fail(ST_ERR_INVALID, "cr_clip must be finite and >= 0");
+  if (opts->tile < -1 || opts->tile > 1 + fast_num_variants())
+    return fail(ST_ERR_INVALID, "tile must be -1 (autotune), 0 (default), 1 (direct-gather "
+                "kernel) or 2..%d (register-window variants)", 1 + fast_num_variants());
   if (opts->pending_capacity < 0 || opts->pending_capacity > (1ll << 31))
     return fail(ST_ERR_INVALID, "pending_capacity must be in [0, 2^31]");
   for (int i = 0; i < n_fields; ++i) {
@@ -329,6 +347,12 @@ st_status st_plan(const st_field* fields, int32_t n_fields, const st_opts* opts,
     if (opts->normalize || opts->storage != ST_F32)
       guard(cudaMalloc(&fp.d_cube, store_bytes(opts->storage) * (size_t)f.n_frames * fp.P()),
             "cudaMalloc(cube)");
+    if (st == ST_OK && opts->tile != 1) {
+      FieldDev probe = field_dev(fp, nullptr, i, opts->storage);
+      if (fast_eligible(probe, opts->mode) && !fast_plan_build(probe, nullptr, nullptr, &fp.fast, p->s))
+        st = fail(ST_ERR_OOM, "field %d: fast-kernel tables could not be allocated", i);
+      if (fp.fast && opts->tile >= 2) fast_set_variant(fp.fast, opts->tile - 2);
+    }
   }
   if (st == ST_OK) {
     p->pend_cap = opts->pending_capacity > 0 ? opts->pending_capacity : (4ll << 20);
@@ -455,9 +479,20 @@ st_status st_dump_stack(st_plan_t* p, int32_t field, const float* d_frames, cons
   CK(cudaMalloc(&d_k, sizeof(int32_t) * n_k));
   cudaError_t e = cudaMemcpyAsync(d_k, h_k, sizeof(int32_t) * n_k, cudaMemcpyHostToDevice, p->s);
   FieldDev fd = field_dev(fp, d_frames, field, p->o.storage);
+  bool whole = n_k == fp.nk();
+  for (int q = 0; q < n_k && whole; ++q) whole = h_k[q] == q;
   if (e == cudaSuccess) {
-    launch_stack_generic(fd, p->o.mode, 0, n_k, d_k, d_S, d_ncov, p->d_pend, p->pend_cap, p->d_ctr,
-                         p->s);
+    int n = -1;
+    if (whole && fp.fast) {
+      bool fits = false;
+      fast_prepare(fd, fp.fast, p->s, &fits);
+      if (fits)
+        n = launch_stack_fast(fd, fp.fast, 0, n_k, nullptr, d_S, d_ncov, p->d_pend, p->pend_cap,
+                              p->d_ctr, p->s);
+    }
+    if (n < 0)
+      launch_stack_generic(fd, p->o.mode, 0, n_k, d_k, d_S, d_ncov, p->d_pend, p->pend_cap,
+                           p->d_ctr, p->s);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->s);
@@ -467,6 +502,11 @@ st_status st_dump_stack(st_plan_t* p, int32_t field, const float* d_frames, cons
 }
 
 int64_t st_last_launch_count(const st_plan_t* p) { return p ? p->launches : 0; }
+
+int32_t st_last_stack_variant(const st_plan_t* p, int32_t field) {
+  if (!p || field < 0 || field >= (int)p->F.size()) return -1;
+  return p->F[field].last_variant;
+}
 
 st_status st_last_stack_kernel_time(const st_plan_t* p, double* ms, int64_t* launches) {
   if (!p || !ms || !launches) return fail(ST_ERR_INVALID, "NULL argument");

@@ -76,6 +76,15 @@ int launch_stack_generic(const FieldDev& fd, int mode, int k0, int nk, const int
 // field's geometry does not fit the kernel (caller falls back).
 struct FastPlan;
 int fast_plan_size_bytes();
+int fast_num_variants();
+const char* fast_variant_name(int v);
+void fast_set_variant(FastPlan* fp, int v);
+// Whether the field can use the fast kernel at all (nearest, FP32 storage,
+// width a multiple of 4).
+bool fast_eligible(const FieldDev& fd, int mode);
+// Builds the per-frame tile tables for the current shift tables; *fits tells
+// whether the motion spans fit the kernel.  Synchronises the stream.
+int fast_prepare(const FieldDev& fd, FastPlan* fp, cudaStream_t s, bool* fits);
 bool fast_plan_build(const FieldDev& fd, const int32_t* h_sx, const int32_t* h_sy,
                      FastPlan** out, cudaStream_t s);
 void fast_plan_free(FastPlan* fp);

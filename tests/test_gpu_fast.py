@@ -1,0 +1,103 @@
+"""GPU parity of the register-window (TMA-staged) nearest-shift stack kernel.
+
+Same bar as the direct-gather kernel: stack values, coverage and candidate
+lists bit-exact with the FP32-sequential oracle (Sec. 2.1 reading of the
+search), on fields with ragged tiles (width not a multiple of 32, height not
+a multiple of 16, velocity counts not multiples of 8), edge tiles, and both
+signs of t - t_ref.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def st():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2303_07293_gb300 as m
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return m
+
+
+VARIANTS = [0, 2, 3, 4, 5]   # plan default and every register-window variant
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def field(seed, W=96, H=45, N=19, nvx=13, nvy=11, dv=0.25, span=2.0, movers=2, ref=None):
+    fr = synth.noise(N, H, W, seed=seed)
+    rng = np.random.default_rng(seed)
+    t = np.sort(rng.uniform(0.0, span, N))
+    t_ref = float(t[N // 3 if ref is None else ref])
+    f = synth.field_params(W, H, N, t_ref, -dv * (nvx // 2) - 0.1, dv, nvx,
+                           -dv * (nvy // 2) + 0.05, dv, nvy, tau=3.5)
+    mv = [[W * 0.3, H * 0.5, 1.0, -0.5, 2.5], [W * 0.7, H * 0.3, -0.75, 0.5, 3.0]][:movers]
+    synth.render_movers(fr, t, f["t_ref"], mv)
+    return fr, t, f
+
+
+@pytest.mark.parametrize("seed,shape", [(1, dict()), (2, dict(W=128, H=64, N=40, nvx=16, nvy=16)),
+                                        (3, dict(W=36, H=17, N=7, nvx=5, nvy=3)),
+                                        (4, dict(W=200, H=33, N=64, nvx=24, nvy=9, dv=0.1))])
+def test_fast_dump_bitexact(st, seed, shape):
+    fr, t, f = field(seed, **shape)
+    ks = np.arange(f["nvx"] * f["nvy"], dtype=np.int32)
+    oS, oC = oracle.stack_planes(fr, t, f, ks, prec="fp32")
+    for tile in VARIANTS:
+        with st.Plan(f, tile=tile) as p:
+            S, Cv = p.dump_stack(0, dev(fr), t, ks)
+            p.candidates(dev(fr), t)
+            assert p.last_stack_variant(0) == 1, "register-window kernel not used"
+        assert np.array_equal(Cv.cpu().numpy(), oC), tile
+        assert np.array_equal(S.cpu().numpy(), oS.astype(np.float32)), tile
+
+
+@pytest.mark.parametrize("seed,shape", [(5, dict()), (6, dict(W=256, H=80, N=48, nvx=33, nvy=17)),
+                                        (7, dict(W=64, H=64, N=30, nvx=8, nvy=8, ref=-1))])
+def test_fast_search_equals_generic_and_oracle(st, seed, shape):
+    fr, t, f = field(seed, **shape)
+    with st.Plan(f) as p:
+        fast = p.candidates(dev(fr), t)
+        assert p.last_stack_variant(0) == 1
+    with st.Plan(f, tile=1) as p:
+        gen = p.candidates(dev(fr), t)
+        assert p.last_stack_variant(0) == 0
+    ref = oracle.search(fr, t, f, prec="fp32")
+    assert len(ref) > 0
+    assert fast.tobytes() == gen.tobytes()
+    assert fast[["x", "y", "k", "n_cov"]].tolist() == ref[["x", "y", "k", "n_cov"]].tolist()
+    assert np.array_equal(fast["stack"], ref["stack"].astype(np.float32))
+
+
+def test_fast_with_normalised_cube(st):
+    d = synth.make_field("mid", width=192, n_frames=24, nv=33, n_movers=5)
+    raw = d["frames"] * 1.5 + 40.0
+    with st.Plan(d["field"], normalize=True) as p:
+        fast = p.candidates(dev(raw), d["times"])
+        assert p.last_stack_variant(0) == 1
+    with st.Plan(d["field"], normalize=True, tile=1) as p:
+        gen = p.candidates(dev(raw), d["times"])
+    assert fast.tobytes() == gen.tobytes() and len(fast) > 0
+
+
+def test_fast_falls_back_when_motion_spans_exceed_window(st):
+    d = synth.make_field("tiny")   # 1 px per frame per grid step: spans too wide
+    with st.Plan(d["field"]) as p:
+        got = p.candidates(dev(d["frames"]), d["times"])
+        assert p.last_stack_variant(0) == 0
+    ref = oracle.search(d["frames"], d["times"], d["field"], prec="fp32")
+    assert got[["x", "y", "k"]].tolist() == ref[["x", "y", "k"]].tolist()
+
+
+def test_add_rate_probe(st):
+    for var in (0, 1, 2):
+        per_clk, t = st.probe_add_rate(var, 4000)
+        assert 16 <= per_clk <= 1024 and t > 1.0, (var, per_clk, t)
