@@ -25,7 +25,7 @@ def st():
     return m
 
 
-VARIANTS = [0, 2, 3, 4, 5]   # plan default and every register-window variant
+VARIANTS = [0, 2, 3, 4, 5, 6]   # plan default and every register-window variant
 
 
 def dev(a):
@@ -45,7 +45,7 @@ def field(seed, W=96, H=45, N=19, nvx=13, nvy=11, dv=0.25, span=2.0, movers=2, r
 
 
 @pytest.mark.parametrize("seed,shape", [(1, dict()), (2, dict(W=128, H=64, N=40, nvx=16, nvy=16)),
-                                        (3, dict(W=36, H=17, N=7, nvx=5, nvy=3)),
+                                        (3, dict(W=36, H=17, N=9, nvx=5, nvy=3)),
                                         (4, dict(W=200, H=33, N=64, nvx=24, nvy=9, dv=0.1))])
 def test_fast_dump_bitexact(st, seed, shape):
     fr, t, f = field(seed, **shape)
@@ -77,6 +77,22 @@ def test_fast_search_equals_generic_and_oracle(st, seed, shape):
     assert np.array_equal(fast["stack"], ref["stack"].astype(np.float32))
 
 
+def test_fast_dense_candidates_every_row(st):
+    # a low threshold puts candidates in every row and velocity slot of every
+    # tile, so each output of a thread's register block is exercised
+    fr, t, f = field(12, W=96, H=100, N=16, nvx=11, nvy=10)
+    f = dict(f, snr_threshold=0.8)
+    ref = oracle.search(fr, t, f, prec="fp32")
+    assert len(ref) > 2000
+    for tile in VARIANTS:
+        with st.Plan(f, tile=tile) as p:
+            got = p.candidates(dev(fr), t)
+            assert p.last_stack_variant(0) == 1
+        assert got[["x", "y", "k", "n_cov"]].tolist() == \
+            ref[["x", "y", "k", "n_cov"]].tolist(), tile
+        assert np.array_equal(got["stack"], ref["stack"].astype(np.float32)), tile
+
+
 def test_fast_with_normalised_cube(st):
     d = synth.make_field("mid", width=192, n_frames=24, nv=33, n_movers=5)
     raw = d["frames"] * 1.5 + 40.0
@@ -86,6 +102,15 @@ def test_fast_with_normalised_cube(st):
     with st.Plan(d["field"], normalize=True, tile=1) as p:
         gen = p.candidates(dev(raw), d["times"])
     assert fast.tobytes() == gen.tobytes() and len(fast) > 0
+
+
+def test_fast_falls_back_for_few_frames(st):
+    fr, t, f = field(11, W=64, H=40, N=6, nvx=9, nvy=9)
+    with st.Plan(f) as p:
+        got = p.candidates(dev(fr), t)
+        assert p.last_stack_variant(0) == 0
+    ref = oracle.search(fr, t, f, prec="fp32")
+    assert got[["x", "y", "k"]].tolist() == ref[["x", "y", "k"]].tolist()
 
 
 def test_fast_falls_back_when_motion_spans_exceed_window(st):
