@@ -37,16 +37,19 @@ METRIC = "G pixel*frame*velocity adds/s (2048x2048x256, 801x801 grid)"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="speculoos", choices=list(WORKLOADS))
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--mode", default="nearest", choices=["nearest", "bilinear"])
     ap.add_argument("--normalize", type=int, default=1)
+    ap.add_argument("--cr-clip", type=float, default=10.0,
+                    help="zero |I| > cr_clip sigma after normalisation (cosmic-ray removal)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tile", type=int, default=0)
     return ap.parse_args()
 
 
@@ -116,6 +119,7 @@ def oracle_baseline(d, seconds, rank0=True):
     """Oracle (FP32-sequential, as it stands) on a slab of velocity planes of
     the same field; returns (adds/s, cores, sample description, elapsed)."""
     import oracle
+    oracle.lib()  # build/load outside the timed region
     f = d["field"]
     N, H, W = d["frames"].shape
     cores = oracle.num_threads()
@@ -157,7 +161,7 @@ def main():
     adds = float(W) * H * N * nk
     config = {"workload": f"{args.workload}: {wl['desc']}", "frames": N, "height": H, "width": W,
               "nv": [f["nvx"], f["nvy"]], "storage": args.storage, "shift": args.mode,
-              "normalize": bool(args.normalize), "tau": f["snr_threshold"],
+              "normalize": bool(args.normalize), "cr_clip": args.cr_clip, "tau": f["snr_threshold"],
               "l2": "inputs larger than L2 (frame cube > 129 MB)"}
 
     if args.impl == "reference":
@@ -193,7 +197,8 @@ def main():
     times = d["times"]
     stream = torch.cuda.current_stream(dev)
     plan = st.Plan(f, storage=args.storage, mode=args.mode, normalize=bool(args.normalize),
-                   stream=stream)
+                   cr_clip=args.cr_clip if args.normalize else 0.0, tile=args.tile,
+                   pending_capacity=1 << 24, stream=stream)
     cap = 1 << 22
     out = torch.empty((cap, 7), dtype=torch.int32, device=dev)
 
@@ -252,7 +257,6 @@ def main():
                 raise RuntimeError(st.lib().st_last_error().decode())
             return cnt.value
 
-        host_step()
         if world > 1:
             torch.distributed.barrier()
         t0 = time.perf_counter()

@@ -71,6 +71,15 @@ struct FastArgs {
   const int32_t* sx;
   const int32_t* sy;
   const float* thr;
+  // coverage prefix tables: for velocity a, covx[a * cov_len + s - cov_xmin[a]]
+  // = number of frames with sx(i, a) <= s (likewise y)
+  const int* covx;
+  const int* covy;
+  const int* cov_xmin;
+  const int* cov_xmax;
+  const int* cov_ymin;
+  const int* cov_ymax;
+  int cov_len;
   Pending* pend;
   int64_t cap;
   Counters* ctr;
@@ -155,6 +164,39 @@ __global__ void k_fast_tables(const int32_t* __restrict__ sx, const int32_t* __r
   }
 }
 
+// Largest spread of one velocity's shifts over the frames (one thread per velocity).
+__global__ void k_shift_spread(const int32_t* __restrict__ sh, int N, int nv, int* out) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nv) return;
+  int mn = INT_MAX, mx = INT_MIN;
+  for (int i = 0; i < N; ++i) {
+    int v = sh[(int64_t)i * nv + a];
+    mn = min(mn, v);
+    mx = max(mx, v);
+  }
+  atomicMax(out, mx - mn + 1);
+}
+
+// Coverage prefix tables of one axis: one thread per velocity.
+__global__ void k_cov_tables(const int32_t* __restrict__ sh, int N, int nv, int len,
+                             int* __restrict__ tab, int* __restrict__ vmin, int* __restrict__ vmax) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nv) return;
+  int mn = INT_MAX, mx = INT_MIN;
+  for (int i = 0; i < N; ++i) {
+    int v = sh[(int64_t)i * nv + a];
+    mn = min(mn, v);
+    mx = max(mx, v);
+  }
+  vmin[a] = mn;
+  vmax[a] = mx;
+  int* row = tab + (int64_t)a * len;
+  int span = mx - mn + 1;  // <= len (checked by the host)
+  for (int s = 0; s < span; ++s) row[s] = 0;
+  for (int i = 0; i < N; ++i) row[sh[(int64_t)i * nv + a] - mn] += 1;
+  for (int s = 1; s < span; ++s) row[s] += row[s - 1];
+}
+
 // acc[j][r] += window[r + C] for the KY rows of a thread, as KY/2 row pairs.
 template <int KY, int C, int M>
 __device__ __forceinline__ void add_rows(float2 (&acc)[KY / 2], const float (&w)[KY + 3]) {
@@ -178,6 +220,13 @@ __device__ __forceinline__ void add_pattern(float2 (&acc)[kMB][KY / 2], const fl
   add_column<KY, pat_off(ID, 1)>(acc[1], w, std::make_integer_sequence<int, KY / 2>{});
   add_column<KY, pat_off(ID, 2)>(acc[2], w, std::make_integer_sequence<int, KY / 2>{});
   add_column<KY, pat_off(ID, 3)>(acc[3], w, std::make_integer_sequence<int, KY / 2>{});
+}
+
+// Number of frames whose shift s satisfies lo <= s <= hi, from a prefix table.
+__device__ __forceinline__ int count_shifts(const int* pre, int smin, int smax, int N, int lo,
+                                            int hi) {
+  auto upto = [&](int s) { return s < smin ? 0 : s >= smax ? N : __ldg(pre + (s - smin)); };
+  return hi < lo ? 0 : upto(hi) - upto(lo - 1);
 }
 
 __device__ int exact_coverage(const FastArgs& p, int x, int y, int av, int bv) {
@@ -386,19 +435,48 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
       // outputs at or above the block's lowest possible threshold, as a
       // bitmask; the exact coverage, threshold and local-maximum test of
       // these rare points happen in the resolver
-      const float thr_lo = __ldg(p.thr + max(n_full, p.nmin));
       constexpr int kWords = (kOut + 31) / 32;
       uint32_t mask[kWords];
 #pragma unroll
       for (int b = 0; b < kWords; ++b) mask[b] = 0u;
+      if (n_full == N) {
+        // interior item: every output is covered by all N frames
+        const float thr_n = __ldg(p.thr + max(N, p.nmin));
 #pragma unroll
-      for (int j = 0; j < kMB; ++j)
+        for (int j = 0; j < kMB; ++j)
 #pragma unroll
-        for (int m = 0; m < KY / 2; ++m) {
-          const int o = j * KY + 2 * m;
-          mask[o / 32] |= (uint32_t)(acc[j][m].x >= thr_lo) << (o % 32);
-          mask[o / 32] |= (uint32_t)(acc[j][m].y >= thr_lo) << (o % 32 + 1);
+          for (int m = 0; m < KY / 2; ++m) {
+            const int o = j * KY + 2 * m;
+            mask[o / 32] |= (uint32_t)(acc[j][m].x >= thr_n) << (o % 32);
+            mask[o / 32] |= (uint32_t)(acc[j][m].y >= thr_n) << (o % 32 + 1);
+          }
+      } else {
+        // edge item: n_cov >= nx + ny - N, with nx / ny the frames whose x / y
+        // sample is inside (ny taken at the item's least covered row), and
+        // n_cov >= n_full; thresholds grow with n_cov, so this never drops a
+        // candidate
+        const int avc = min(av, p.nvx - 1);
+        const int nx = count_shifts(p.covx + (int64_t)avc * p.cov_len, __ldg(p.cov_xmin + avc),
+                                    __ldg(p.cov_xmax + avc), N, -x, p.W - 1 - x);
+#pragma unroll
+        for (int j = 0; j < kMB; ++j) {
+          // ny minimised over the item's rows (lane l takes row l % KY)
+          const int bvc = min(it.B * kMB + j, p.nvy - 1);
+          const int y = it.Y0 + lane % KY;
+          int ny = count_shifts(p.covy + (int64_t)bvc * p.cov_len, __ldg(p.cov_ymin + bvc),
+                                __ldg(p.cov_ymax + bvc), N, -y, p.H - 1 - y);
+#pragma unroll
+          for (int d = 16; d > 0; d >>= 1) ny = min(ny, __shfl_xor_sync(0xffffffffu, ny, d));
+          const int nlo = max(max(n_full, p.nmin), nx + ny - N);
+          const float thr_j = __ldg(p.thr + min(nlo, N));
+#pragma unroll
+          for (int m = 0; m < KY / 2; ++m) {
+            const int o = j * KY + 2 * m;
+            mask[o / 32] |= (uint32_t)(acc[j][m].x >= thr_j) << (o % 32);
+            mask[o / 32] |= (uint32_t)(acc[j][m].y >= thr_j) << (o % 32 + 1);
+          }
         }
+      }
       const bool col_ok = x < p.W && av < p.nvx;
       for (int b = 0; b < kWords; ++b) {
         uint32_t mk = col_ok ? mask[b] : 0u;
@@ -475,6 +553,9 @@ struct FastPlan {
   int4* yt = nullptr;
   int* ranges = nullptr;  // xmin[nA], xmax[nA], ymin[nB], ymax[nB], maxes[2]
   int* h_maxes = nullptr; // pinned
+  int* cov = nullptr;     // covx [nvx*len], covy [nvy*len], mins/maxes [2*nvx + 2*nvy]
+  int cov_len = 0;
+  int64_t cov_cap = 0;
 };
 
 int fast_plan_size_bytes() { return (int)sizeof(FastPlan); }
@@ -500,8 +581,8 @@ bool fast_plan_build(const FieldDev& fd, const int32_t*, const int32_t*, FastPla
   fp->N = fd.N;
   bool good = cudaMalloc(&fp->xt, sizeof(int4) * (size_t)fd.N * fp->nA) == cudaSuccess &&
               cudaMalloc(&fp->yt, sizeof(int4) * (size_t)fd.N * fp->nB) == cudaSuccess &&
-              cudaMalloc(&fp->ranges, sizeof(int) * (2 * fp->nA + 2 * fp->nB + 2)) == cudaSuccess &&
-              cudaMallocHost(&fp->h_maxes, sizeof(int) * 2) == cudaSuccess &&
+              cudaMalloc(&fp->ranges, sizeof(int) * (2 * fp->nA + 2 * fp->nB + 3)) == cudaSuccess &&
+              cudaMallocHost(&fp->h_maxes, sizeof(int) * 3) == cudaSuccess &&
               cudaMalloc(&fp->d_pat, (size_t)fd.N * fp->nB) == cudaSuccess &&
               cudaMallocHost(&fp->h_pat, (size_t)fd.N * fp->nB) == cudaSuccess;
   if (!good) {
@@ -517,6 +598,7 @@ void fast_plan_free(FastPlan* fp) {
   cudaFree(fp->xt);
   cudaFree(fp->yt);
   cudaFree(fp->ranges);
+  cudaFree(fp->cov);
   if (fp->h_maxes) cudaFreeHost(fp->h_maxes);
   cudaFree(fp->d_pat);
   if (fp->h_pat) cudaFreeHost(fp->h_pat);
@@ -538,14 +620,37 @@ int fast_prepare(const FieldDev& fd, FastPlan* fp, cudaStream_t s, bool* fits) {
   cudaMemsetAsync(xmax, 0x80, sizeof(int) * nA, s);
   cudaMemsetAsync(ymin, 0x7f, sizeof(int) * nB, s);
   cudaMemsetAsync(ymax, 0x80, sizeof(int) * nB, s);
-  cudaMemsetAsync(maxes, 0, sizeof(int) * 2, s);
+  cudaMemsetAsync(maxes, 0, sizeof(int) * 3, s);
   int64_t n = (int64_t)fd.N * (nA + nB);
   k_fast_tables<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(fd.sx, fd.sy, fd.N, fd.nvx, fd.nvy, nA,
                                                             nB, fp->xt, fp->yt, xmin, xmax, ymin,
                                                             ymax, maxes, fp->d_pat);
-  cudaMemcpyAsync(fp->h_maxes, maxes, sizeof(int) * 2, cudaMemcpyDeviceToHost, s);
+  k_shift_spread<<<(fd.nvx + 127) / 128, 128, 0, s>>>(fd.sx, fd.N, fd.nvx, maxes + 2);
+  k_shift_spread<<<(fd.nvy + 127) / 128, 128, 0, s>>>(fd.sy, fd.N, fd.nvy, maxes + 2);
+  cudaMemcpyAsync(fp->h_maxes, maxes, sizeof(int) * 3, cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(fp->h_pat, fp->d_pat, (size_t)fd.N * nB, cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return 1;
+  // coverage prefix tables: one row per velocity, as long as the widest spread
+  const int len = fp->h_maxes[2];
+  const int64_t need = (int64_t)(fd.nvx + fd.nvy) * (len + 2);
+  if (len <= 0 || need > (64ll << 20)) return 1;  // tables too large: generic kernel
+  if (need > fp->cov_cap) {
+    cudaFree(fp->cov);
+    fp->cov = nullptr;
+    fp->cov_cap = 0;
+    if (cudaMalloc(&fp->cov, sizeof(int) * need) != cudaSuccess) return 1;
+    fp->cov_cap = need;
+  }
+  fp->cov_len = len;
+  int* covx = fp->cov;
+  int* covy = covx + (int64_t)fd.nvx * len;
+  int* cxmin = covy + (int64_t)fd.nvy * len;
+  int* cxmax = cxmin + fd.nvx;
+  int* cymin = cxmax + fd.nvx;
+  int* cymax = cymin + fd.nvy;
+  k_cov_tables<<<(fd.nvx + 127) / 128, 128, 0, s>>>(fd.sx, fd.N, fd.nvx, len, covx, cxmin, cxmax);
+  k_cov_tables<<<(fd.nvy + 127) / 128, 128, 0, s>>>(fd.sy, fd.N, fd.nvy, len, covy, cymin, cymax);
+  if (cudaGetLastError() != cudaSuccess) return 1;
   // N >= 8: the producer runs at most S*F = 24 frames ahead of the consumers,
   // so at most 4 items are live and the 8 per-item slots never collide.
   *fits = fp->h_maxes[0] <= kOColMax && fp->h_maxes[1] < kPatterns && fd.N <= kParamBytes &&
@@ -601,6 +706,13 @@ int launch_stack_fast(const FieldDev& fd, const FastPlan* cfp, int k0, int nk,
   a.sx = fd.sx;
   a.sy = fd.sy;
   a.thr = fd.thr;
+  a.cov_len = fp->cov_len;
+  a.covx = fp->cov;
+  a.covy = fp->cov + (int64_t)fd.nvx * fp->cov_len;
+  a.cov_xmin = a.covy + (int64_t)fd.nvy * fp->cov_len;
+  a.cov_xmax = a.cov_xmin + fd.nvx;
+  a.cov_ymin = a.cov_xmax + fd.nvx;
+  a.cov_ymax = a.cov_ymin + fd.nvy;
   a.pend = pend;
   a.cap = pend_cap;
   a.ctr = ctr;
