@@ -42,9 +42,8 @@ def lib():
             C.c_int, C.c_int, C.c_float, C.c_int, C.c_int32, C.c_int32, P, C.c_int64]
         L.oracle_search.restype = C.c_int64
         L.oracle_num_threads.restype = C.c_int
-        if hasattr(L, "oracle_refine_eval"):
-            L.oracle_refine_eval.argtypes = [P, C.c_int, C.c_int, C.c_int, P, C.c_double, P, P,
-                                             C.c_int64, C.c_double, P, P, P]
+        L.oracle_refine_eval.argtypes = [P, C.c_int, C.c_int, C.c_int, P, C.c_double, P, P,
+                                         C.c_int64, C.c_double, P, P, P]
         _lib = L
     return _lib
 
@@ -162,3 +161,20 @@ def search(frames, t, field, mode="nearest", prec="fp32", k_begin=0, k_end=None,
                    ("stack", np.float64), ("snr", np.float64)])
     arr = np.frombuffer(bytearray(buf), dtype=dt, count=min(n, cap)).copy()
     return arr
+
+
+def refine_eval(frames, t, t_ref, theta, centre, fwhm=3.0, grad=True):
+    """FP64 refinement objective: J [n], SNR [n] and dJ/dtheta [n][5]
+    (theta rows: vx, vy, x0, y0, F; centre rows: integer cutout centre)."""
+    frames = _f32(frames)
+    t = _f64(t)
+    N, H, W = frames.shape
+    th = _f64(theta).reshape(-1, 5)
+    ce = np.ascontiguousarray(centre, np.int32).reshape(-1, 2)
+    n = len(th)
+    J = np.zeros(n)
+    snr = np.zeros(n)
+    g = np.zeros((n, 5)) if grad else None
+    lib().oracle_refine_eval(_p(frames), N, H, W, _p(t), float(t_ref), _p(th), _p(ce), n,
+                             float(fwhm), _p(J), _p(snr), _p(g) if grad else None)
+    return J, snr, g
