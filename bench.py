@@ -30,6 +30,8 @@ WORKLOADS = {
     "speculoos": dict(name="speculoos", desc="2048x2048x256, 801x801 velocity grid"),
     "mid": dict(name="mid", desc="1024x1024x64, 161x161 velocity grid"),
     "tiny": dict(name="tiny", desc="128x128x16, 21x21 velocity grid"),
+    "batched": dict(name="batched", desc="24 fields: N in [40,400], sizes {512,1024,2048}^2, "
+                    "baselines 1-8 h, grid step 1 px/baseline, +-60 px/h, one plan"),
 }
 METRIC = "G pixel*frame*velocity adds/s (2048x2048x256, 801x801 grid)"
 
@@ -49,7 +51,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--tile", type=int, default=-1,
+                    help="-1 autotune (first warm-up step), 0 default, 1 direct-gather, 2.. variant")
     return ap.parse_args()
 
 
@@ -144,7 +147,9 @@ def oracle_baseline(d, seconds, rank0=True):
 def field_for(args, rank):
     import synth
     w = WORKLOADS[args.workload]["name"]
-    seed = synth.BASE_SEED + {"tiny": 1, "mid": 2, "speculoos": 3}[w] + 1000 * rank
+    seed = synth.BASE_SEED + {"tiny": 1, "mid": 2, "speculoos": 3, "batched": 4}[w] + 100000 * rank
+    if w == "batched":
+        return [synth.make_field(w, seed=seed, index=j) for j in range(24)]
     return synth.make_field(w, seed=seed)
 
 
@@ -155,14 +160,19 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     wl = WORKLOADS[args.workload]
     d = field_for(args, rank)
+    ds = d if isinstance(d, list) else [d]
+    d = ds[0]
     f = d["field"]
     N, H, W = d["frames"].shape
-    nk = f["nvx"] * f["nvy"]
-    adds = float(W) * H * N * nk
+    adds = sum(float(x["frames"].size) * x["field"]["nvx"] * x["field"]["nvy"] for x in ds)
     config = {"workload": f"{args.workload}: {wl['desc']}", "frames": N, "height": H, "width": W,
               "nv": [f["nvx"], f["nvy"]], "storage": args.storage, "shift": args.mode,
               "normalize": bool(args.normalize), "cr_clip": args.cr_clip, "tau": f["snr_threshold"],
-              "l2": "inputs larger than L2 (frame cube > 129 MB)"}
+              "tile": args.tile, "l2": "inputs larger than L2 (frame cube > 129 MB)"}
+    if len(ds) > 1:
+        config.update({"fields": len(ds), "frames": [x["frames"].shape[0] for x in ds],
+                       "sizes": [x["frames"].shape[1] for x in ds],
+                       "nv": [x["field"]["nvx"] for x in ds], "adds_per_step": adds})
 
     if args.impl == "reference":
         if rank != 0:
@@ -193,10 +203,10 @@ def main():
     dev = torch.device("cuda", local)
     import paper_2303_07293_gb300 as st
 
-    frames = torch.from_numpy(d["frames"]).to(dev)
-    times = d["times"]
+    frames = [torch.from_numpy(x["frames"]).to(dev) for x in ds]
+    times = [x["times"] for x in ds]
     stream = torch.cuda.current_stream(dev)
-    plan = st.Plan(f, storage=args.storage, mode=args.mode, normalize=bool(args.normalize),
+    plan = st.Plan([x["field"] for x in ds], storage=args.storage, mode=args.mode, normalize=bool(args.normalize),
                    cr_clip=args.cr_clip if args.normalize else 0.0, tile=args.tile,
                    pending_capacity=1 << 24, stream=stream)
     cap = 1 << 22
@@ -240,12 +250,12 @@ def main():
     # end to end through the host-buffer entry point (pinned frames)
     e2e = None
     if not args.no_e2e:
-        hframes = torch.from_numpy(d["frames"]).pin_memory()
+        hframes = [torch.from_numpy(x["frames"]).pin_memory() for x in ds]
         hbuf = np.zeros(cap, st.CAND_DTYPE)
         import ctypes as C
-        fptr = (C.c_void_p * 1)(hframes.data_ptr())
-        tarr = np.ascontiguousarray(times, np.float64)
-        tptr = (C.c_void_p * 1)(tarr.ctypes.data)
+        fptr = (C.c_void_p * len(ds))(*[h.data_ptr() for h in hframes])
+        tarr = [np.ascontiguousarray(t_, np.float64) for t_ in times]
+        tptr = (C.c_void_p * len(ds))(*[t_.ctypes.data for t_ in tarr])
         cnt = C.c_int64()
 
         def host_step():
@@ -268,7 +278,8 @@ def main():
             torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
             te = float(tt.item())
         e2e = {"value": adds * world / te / 1e9, "unit": "G adds/s",
-               "h2d_bytes_per_step": int(hframes.numel() * 4 + tarr.nbytes),
+               "h2d_bytes_per_step": int(sum(h.numel() * 4 for h in hframes) +
+                                         sum(t_.nbytes for t_ in tarr)),
                "d2h_bytes_per_step": int(nh * 28 + 32), "s_per_step": te}
 
     if rank != 0:

@@ -234,6 +234,40 @@ class Plan:
                                    ks.size, _ptr(S), _ptr(Cv)))
         return S, Cv
 
+    # ------------------------------------------------------------ refinement
+    def refine(self, cands, n=None, steps=20, fwhm=3.0, lr_pos=0.05, lr_vel=None, grad=False):
+        """st_refine: Adam refinement of candidates (device tensor [n, 7] int32 as
+        returned by search).  Returns the refined records (numpy) and, if grad,
+        dJ/dtheta [n, 5] at the final parameters."""
+        import torch
+        n = cands.shape[0] if n is None else n
+        if lr_vel is None:
+            lr_vel = 0.05 * float(self.fields[0]["dvx"])
+        out = torch.empty((max(n, 1), 8), dtype=torch.int32, device=cands.device)
+        g = torch.empty((max(n, 1), 5), dtype=torch.float32, device=cands.device) if grad else None
+        _check(lib().st_refine(self._h, _ptr(cands), n, steps, 0, fwhm, lr_pos, lr_vel, _ptr(out),
+                               _ptr(g) if grad else None))
+        rec = out[:n].cpu().numpy().view(REFINED_DTYPE).reshape(-1)
+        return (rec, g[:n]) if grad else rec
+
+    def refine_eval(self, theta, centre, field=None, fwhm=3.0, grad=True):
+        """st_refine_eval: J [n], SNR [n] and (optionally) dJ/dtheta [n, 5] at
+        theta ([n, 5] float32 CUDA: vx, vy, x0, y0, F), cutout centres [n, 2]."""
+        import torch
+        theta = theta.detach().contiguous().float()
+        n = theta.shape[0]
+        dev_ = theta.device
+        centre = torch.as_tensor(centre, dtype=torch.int32, device=dev_).contiguous()
+        if field is None:
+            field = torch.zeros(n, dtype=torch.int32, device=dev_)
+        field = torch.as_tensor(field, dtype=torch.int32, device=dev_).contiguous()
+        J = torch.empty(n, dtype=torch.float32, device=dev_)
+        snr = torch.empty(n, dtype=torch.float32, device=dev_)
+        g = torch.empty((n, 5), dtype=torch.float32, device=dev_) if grad else None
+        _check(lib().st_refine_eval(self._h, _ptr(theta), _ptr(centre), _ptr(field), n, fwhm,
+                                    _ptr(J), _ptr(snr), _ptr(g) if grad else None))
+        return J, snr, g
+
     def last_stack_variant(self, field=0):
         """1 if field used the register-window kernel in the last search, 0 if
         the direct-gather kernel, -1 before any search."""
@@ -247,6 +281,35 @@ class Plan:
         n = C.c_int64()
         _check(lib().st_last_stack_kernel_time(self._h, C.byref(ms), C.byref(n)))
         return ms.value, n.value
+
+
+def _refine_objective_class():
+    import torch
+
+    class RefineObjective(torch.autograd.Function):
+        """J(theta) of the refinement on a plan's last searched frames.  The
+        backward pass calls the library's hand-written adjoint, recomputing the
+        shifted cutouts instead of storing them."""
+
+        @staticmethod
+        def forward(ctx, theta, plan, centre, field, fwhm):
+            J, _, _ = plan.refine_eval(theta, centre, field, fwhm, grad=False)
+            ctx.save_for_backward(theta.detach())
+            ctx.plan, ctx.centre, ctx.field, ctx.fwhm = plan, centre, field, fwhm
+            return J
+
+        @staticmethod
+        def backward(ctx, gJ):
+            (theta,) = ctx.saved_tensors
+            _, _, g = ctx.plan.refine_eval(theta, ctx.centre, ctx.field, ctx.fwhm, grad=True)
+            return gJ[:, None] * g, None, None, None, None
+
+    return RefineObjective
+
+
+def refine_objective(theta, plan, centre, field=None, fwhm=3.0):
+    """Differentiable J(theta) (torch.autograd) with the library's adjoint."""
+    return _refine_objective_class().apply(theta, plan, centre, field, fwhm)
 
 
 def probe_add_rate(variant=1, iters=20000):

@@ -30,6 +30,8 @@
 // kernel (out-of-frame samples add +0.0 from the TMA zero fill, which leaves
 // any sum unchanged), so the two kernels agree bit for bit.
 #include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -48,8 +50,28 @@ namespace {
 constexpr int kXV = 8;           // x-velocities per block, one per warp (within a row group)
 constexpr int kMB = 4;           // y-velocities per block (staircase group)
 constexpr int kTX = 32;          // pixel tile width; its height is the variant's KY
-constexpr int kBoxW = 40;        // shared row pitch and TMA box width (floats)
-constexpr int kOColMax = kBoxW - kTX;  // largest column offset of a warp
+// Storage traits: TMA box width (elements; 16-byte rows), x alignment of the
+// box origin (16 bytes), and the largest column offset of a warp.
+template <typename T>
+struct Store;
+template <>
+struct Store<float> {
+  static constexpr int kBoxW = 40, kAlign = 4, kOColMax = 8;
+  static constexpr CUtensorMapDataType kTma = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  __device__ static float f(float v) { return v; }
+};
+template <>
+struct Store<__half> {
+  static constexpr int kBoxW = 48, kAlign = 8, kOColMax = 15;
+  static constexpr CUtensorMapDataType kTma = CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  __device__ static float f(__half v) { return __half2float(v); }
+};
+template <>
+struct Store<__nv_bfloat16> {
+  static constexpr int kBoxW = 48, kAlign = 8, kOColMax = 15;
+  static constexpr CUtensorMapDataType kTma = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  __device__ static float f(__nv_bfloat16 v) { return __bfloat162float(v); }
+};
 constexpr int kSuper = 4;        // pixel tiles per super-tile side (L2 locality)
 constexpr uint64_t kWaitNs = 2000000000ull;  // wait limit: 2 s of wall-clock time
 constexpr int kParamBytes = 28672;  // staircase pattern ids carried in the kernel parameters
@@ -115,7 +137,7 @@ __device__ int pattern_of(const int (&c)[kMB]) {
 __global__ void k_fast_tables(const int32_t* __restrict__ sx, const int32_t* __restrict__ sy,
                               int N, int nvx, int nvy, int nA, int nB, int4* __restrict__ xt,
                               int4* __restrict__ yt, int* xmin, int* xmax, int* ymin, int* ymax,
-                              int* maxes, unsigned char* __restrict__ pat) {
+                              int* maxes, unsigned char* __restrict__ pat, int align) {
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t nX = (int64_t)N * nA, nY = (int64_t)N * nB;
   if (idx < nX) {
@@ -128,7 +150,7 @@ __global__ void k_fast_tables(const int32_t* __restrict__ sx, const int32_t* __r
       mn = min(mn, s[j]);
       mx = max(mx, s[j]);
     }
-    int xs = mn & ~3;  // 16-byte aligned box origin (floor to a multiple of 4)
+    int xs = mn & ~(align - 1);  // 16-byte aligned box origin (floor to a multiple of align)
     uint32_t packed = 0;
     int om = 0;
 #pragma unroll
@@ -271,9 +293,10 @@ __device__ __forceinline__ Item decode_item(const FastArgs& p, int64_t L) {
 // parameters through a warp-uniform index, so its switch is a uniform
 // branch.  A ring of S stages runs continuously across items.  Every wait is
 // bounded in time.
-template <int KY, int S, int F, bool DUMP>
+template <typename T, int KY, int S, int F, bool DUMP>
 __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
     k_stack_fast(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ FastArgs p) {
+  constexpr int kBoxW = Store<T>::kBoxW;
   constexpr int kTY = KY;         // tile height: one row group of KY rows per thread
   constexpr int kBoxH = KY + 3;   // tile rows + largest staircase offset
   constexpr int kCW = kXV;        // consumer warps
@@ -287,10 +310,11 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
   __shared__ uint32_t slot_ocol[S * F];     // packed 4-bit column offsets of the 8 warps
   __shared__ int item_inside[kItemSlots];   // frames of an item fully inside the frame
 
-  float* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u) / sizeof(float);
+  T* smem = reinterpret_cast<T*>(reinterpret_cast<char*>(smem_raw) +
+                                 ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t box_bytes = (uint32_t)kBoxH * kBoxW * sizeof(float);
-  const int box_floats = p.stage_floats;  // one frame's box, 128-byte aligned
+  const uint32_t box_bytes = (uint32_t)kBoxH * kBoxW * sizeof(T);
+  const int box_floats = p.stage_floats;  // one frame's box in elements, 128-byte aligned
   const int N = p.N;
   const int spi = (N + F - 1) / F;       // stages per item
   const int G = (int)gridDim.x;
@@ -371,15 +395,15 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
         ok = false;
         break;
       }
-      const float* stage = smem + (size_t)(c_slot * F) * box_floats + lane;
+      const T* stage = smem + (size_t)(c_slot * F) * box_floats + lane;
       for (int fi = 0; fi < F; ++fi) {
         const int f = st * F + fi;
         const int id = f < N ? (int)pat[f] : kNoop;
         const int ocol = (slot_ocol[c_slot * F + fi] >> (4 * xw)) & 15u;
-        const float* col = stage + fi * box_floats + ocol;
+        const T* col = stage + fi * box_floats + ocol;
         float w[KY + 3];
 #pragma unroll
-        for (int r = 0; r < KY + 3; ++r) w[r] = col[r * kBoxW];
+        for (int r = 0; r < KY + 3; ++r) w[r] = Store<T>::f(col[r * kBoxW]);
         if (fi == F - 1) {
           __syncwarp();
           if (lane == 0) mbar_arrive(&empty_bar[c_slot]);
@@ -508,16 +532,33 @@ struct Variant {
   const char* name;
 };
 
-#define ST_VARIANT(KY, S, F)                                                                  \
+#define ST_VARIANT(T, KY, S, F)                                                               \
   {                                                                                           \
-    (void (*)(CUtensorMap, FastArgs))k_stack_fast<KY, S, F, false>,                             \
-        (void (*)(CUtensorMap, FastArgs))k_stack_fast<KY, S, F, true>, 32 * (kXV + 1), S * F, KY, \
-        "ky" #KY "_s" #S "_f" #F                                                              \
+    (void (*)(CUtensorMap, FastArgs))k_stack_fast<T, KY, S, F, false>,                          \
+        (void (*)(CUtensorMap, FastArgs))k_stack_fast<T, KY, S, F, true>, 32 * (kXV + 1), S * F,   \
+        KY, #T "_ky" #KY "_s" #S "_f" #F                                                       \
   }
-const Variant kVariants[] = {ST_VARIANT(16, 6, 4), ST_VARIANT(16, 8, 4), ST_VARIANT(20, 6, 4),
-                             ST_VARIANT(24, 6, 4), ST_VARIANT(16, 12, 2)};
+const Variant kVarF32[] = {ST_VARIANT(float, 16, 6, 4), ST_VARIANT(float, 16, 8, 4),
+                           ST_VARIANT(float, 20, 6, 4), ST_VARIANT(float, 24, 6, 4),
+                           ST_VARIANT(float, 16, 12, 2)};
+const Variant kVarF16[] = {ST_VARIANT(__half, 16, 6, 4), ST_VARIANT(__half, 16, 8, 4)};
+const Variant kVarBF16[] = {ST_VARIANT(__nv_bfloat16, 16, 6, 4),
+                            ST_VARIANT(__nv_bfloat16, 16, 8, 4)};
 #undef ST_VARIANT
-constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+constexpr int kNumVariants = sizeof(kVarF32) / sizeof(kVarF32[0]);  // the largest list
+
+const Variant* variants_for(int storage, int* count) {
+  if (storage == ST_F16) {
+    *count = sizeof(kVarF16) / sizeof(kVarF16[0]);
+    return kVarF16;
+  }
+  if (storage == ST_BF16) {
+    *count = sizeof(kVarBF16) / sizeof(kVarBF16[0]);
+    return kVarBF16;
+  }
+  *count = kNumVariants;
+  return kVarF32;
+}
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
@@ -545,7 +586,8 @@ struct FastPlan {
   CUtensorMap tmap;
   const void* encoded_for = nullptr;
   int encoded_boxh = 0;
-  int variant = 0;  // index into kVariants
+  int variant = 0;         // index into the storage type's variant list
+  int64_t item_limit = 0;  // > 0: run only the first item_limit items (autotuning)
   int nA = 0, nB = 0, N = 0;
   unsigned char* d_pat = nullptr;  // [N][nB] pattern ids
   unsigned char* h_pat = nullptr;  // pinned copy for the kernel parameters
@@ -561,13 +603,61 @@ struct FastPlan {
 int fast_plan_size_bytes() { return (int)sizeof(FastPlan); }
 
 int fast_num_variants() { return kNumVariants; }
-const char* fast_variant_name(int v) { return v >= 0 && v < kNumVariants ? kVariants[v].name : "?"; }
+
+int fast_num_variants_for(int storage) {
+  int n = 0;
+  variants_for(storage, &n);
+  return n;
+}
+
+int fast_get_variant(const FastPlan* fp) { return fp ? fp->variant : -1; }
+
+// Times the register-window variants on the first `items` work items and
+// keeps the fastest.  Pushes to the pending list (callers reset counters).
+int fast_autotune(const FieldDev& fd, FastPlan* fp, int64_t items, Pending* pend,
+                  int64_t pend_cap, Counters* ctr, cudaStream_t s) {
+  int n = 0;
+  variants_for(fd.storage, &n);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int best_v = fp->variant;
+  int launches = 0;
+  fp->item_limit = items;
+  for (int v = 0; v < n; ++v) {
+    fp->variant = v;
+    float ms_min = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {  // first run warms up
+      cudaEventRecord(e0, s);
+      int l = launch_stack_fast(fd, fp, 0, fd.nvx * fd.nvy, nullptr, nullptr, nullptr, pend,
+                                pend_cap, ctr, s);
+      cudaEventRecord(e1, s);
+      if (l < 0 || cudaEventSynchronize(e1) != cudaSuccess) break;
+      launches += l;
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0 && ms < ms_min) ms_min = ms;
+    }
+    if (ms_min < best) {
+      best = ms_min;
+      best_v = v;
+    }
+  }
+  fp->item_limit = 0;
+  fp->variant = best_v;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return launches;
+}
+const char* fast_variant_name(int v) { return v >= 0 && v < kNumVariants ? kVarF32[v].name : "?"; }
 void fast_set_variant(FastPlan* fp, int v) {
   if (fp && v >= 0 && v < kNumVariants) fp->variant = v;
 }
 
 bool fast_eligible(const FieldDev& fd, int mode) {
-  return mode == ST_NEAREST && fd.storage == ST_F32 && fd.W % 4 == 0 && encode_fn() != nullptr &&
+  const int align = fd.storage == ST_F32 ? 4 : 8;  // 16-byte rows for the tensor map
+  return mode == ST_NEAREST && fd.W % align == 0 && encode_fn() != nullptr &&
          fd.W >= 8 && fd.H >= 1;
 }
 
@@ -624,7 +714,8 @@ int fast_prepare(const FieldDev& fd, FastPlan* fp, cudaStream_t s, bool* fits) {
   int64_t n = (int64_t)fd.N * (nA + nB);
   k_fast_tables<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(fd.sx, fd.sy, fd.N, fd.nvx, fd.nvy, nA,
                                                             nB, fp->xt, fp->yt, xmin, xmax, ymin,
-                                                            ymax, maxes, fp->d_pat);
+                                                            ymax, maxes, fp->d_pat,
+                                                            fd.storage == ST_F32 ? 4 : 8);
   k_shift_spread<<<(fd.nvx + 127) / 128, 128, 0, s>>>(fd.sx, fd.N, fd.nvx, maxes + 2);
   k_shift_spread<<<(fd.nvy + 127) / 128, 128, 0, s>>>(fd.sy, fd.N, fd.nvy, maxes + 2);
   cudaMemcpyAsync(fp->h_maxes, maxes, sizeof(int) * 3, cudaMemcpyDeviceToHost, s);
@@ -653,7 +744,8 @@ int fast_prepare(const FieldDev& fd, FastPlan* fp, cudaStream_t s, bool* fits) {
   if (cudaGetLastError() != cudaSuccess) return 1;
   // N >= 8: the producer runs at most S*F = 24 frames ahead of the consumers,
   // so at most 4 items are live and the 8 per-item slots never collide.
-  *fits = fp->h_maxes[0] <= kOColMax && fp->h_maxes[1] < kPatterns && fd.N <= kParamBytes &&
+  const int ocol_max = fd.storage == ST_F32 ? Store<float>::kOColMax : Store<__half>::kOColMax;
+  *fits = fp->h_maxes[0] <= ocol_max && fp->h_maxes[1] < kPatterns && fd.N <= kParamBytes &&
           fd.N >= 8;
   return 1;
 }
@@ -663,14 +755,21 @@ int launch_stack_fast(const FieldDev& fd, const FastPlan* cfp, int k0, int nk,
                       int64_t pend_cap, Counters* ctr, cudaStream_t s) {
   FastPlan* fp = const_cast<FastPlan*>(cfp);
   if (k0 != 0 || nk != fd.nvx * fd.nvy || dump_k) return -1;  // whole grid only
-  const Variant& var = kVariants[fp->variant];
+  int nvar = 0;
+  const Variant* vars = variants_for(fd.storage, &nvar);
+  const Variant& var = vars[fp->variant < nvar ? fp->variant : 0];
   const int ky = var.ky, boxh = ky + 3;
+  const int esz = fd.storage == ST_F32 ? 4 : 2;
+  const int boxw = fd.storage == ST_F32 ? Store<float>::kBoxW : Store<__half>::kBoxW;
+  const CUtensorMapDataType dtype = fd.storage == ST_F32    ? Store<float>::kTma
+                                    : fd.storage == ST_F16 ? Store<__half>::kTma
+                                                           : Store<__nv_bfloat16>::kTma;
   if (fp->encoded_for != fd.cube || fp->encoded_boxh != boxh) {
     cuuint64_t dims[3] = {(cuuint64_t)fd.W, (cuuint64_t)fd.H, (cuuint64_t)fd.N};
-    cuuint64_t strides[2] = {(cuuint64_t)fd.W * 4, (cuuint64_t)fd.W * fd.H * 4};
-    cuuint32_t box[3] = {(cuuint32_t)kBoxW, (cuuint32_t)boxh, 1};
+    cuuint64_t strides[2] = {(cuuint64_t)fd.W * esz, (cuuint64_t)fd.W * fd.H * esz};
+    cuuint32_t box[3] = {(cuuint32_t)boxw, (cuuint32_t)boxh, 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = encode_fn()(&fp->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+    CUresult r = encode_fn()(&fp->tmap, dtype, 3,
                              const_cast<void*>(fd.cube), dims, strides, box, estr,
                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -688,8 +787,8 @@ int launch_stack_fast(const FieldDev& fd, const FastPlan* cfp, int k0, int nk,
   a.nvy = fd.nvy;
   a.nA = fp->nA;
   a.nB = fp->nB;
-  int stage_bytes = ((boxh * kBoxW * 4) + 127) & ~127;
-  a.stage_floats = stage_bytes / 4;
+  int stage_bytes = ((boxh * boxw * esz) + 127) & ~127;
+  a.stage_floats = stage_bytes / esz;
   a.ty_rows = ky;
   a.tiles_x = (fd.W + kTX - 1) / kTX;
   a.tiles_y = (fd.H + ky - 1) / ky;
@@ -720,11 +819,11 @@ int launch_stack_fast(const FieldDev& fd, const FastPlan* cfp, int k0, int nk,
   a.dump_C = dump_C;
   void (*fn)(CUtensorMap, FastArgs) = dump_S ? var.dump_fn : var.fn;
   size_t smem = (size_t)var.stages * stage_bytes + 128;
-  static bool attr_set[2 * kNumVariants] = {};
-  const int attr_i = 2 * fp->variant + (dump_S ? 1 : 0);
-  if (!attr_set[attr_i]) {
+  static bool attr_set[3][2 * kNumVariants] = {};
+  const int attr_i = 2 * (fp->variant < nvar ? fp->variant : 0) + (dump_S ? 1 : 0);
+  if (!attr_set[fd.storage][attr_i]) {
     cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set[attr_i] = true;
+    attr_set[fd.storage][attr_i] = true;
   }
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -733,11 +832,13 @@ int launch_stack_fast(const FieldDev& fd, const FastPlan* cfp, int k0, int nk,
   if (G < 1) return -1;
   int launches = 0;
   for (int B0 = 0; B0 < fp->nB; B0 += G) {
+    if (fp->item_limit > 0 && B0 > 0) break;  // autotuning samples the first launch only
     a.B0 = B0;
     a.G = fp->nB - B0 < G ? fp->nB - B0 : G;
     for (int g = 0; g < a.G; ++g)
       for (int i = 0; i < fd.N; ++i) a.pat[g * fd.N + i] = fp->h_pat[(size_t)i * fp->nB + B0 + g];
     a.n_items = (int64_t)a.super_x * a.super_y * kSuper * kSuper * a.nA * a.G;
+    if (fp->item_limit > 0 && a.n_items > fp->item_limit) a.n_items = fp->item_limit;
     const int per_sm = ky <= 16 ? 2 : 1;  // persistent CTAs per SM
     const int64_t grid = a.n_items < (int64_t)sms * per_sm ? a.n_items : (int64_t)sms * per_sm;
     void* args[2] = {&fp->tmap, &a};

@@ -72,6 +72,7 @@ struct FieldPlan {
   float* d_frames_copy = nullptr; // device copy for the host-buffer entry point
   FastPlan* fast = nullptr;
   int last_variant = -1;
+  bool tuned = false;
   const float* last_frames = nullptr;
   int64_t P() const { return (int64_t)f.width * f.height; }
   int64_t nk() const { return (int64_t)f.nvx * f.nvy; }
@@ -91,10 +92,15 @@ struct st_plan_s {
   uint32_t* d_idx = nullptr;
   int64_t sort_cap = 0;
   FieldDev* d_fds = nullptr;
+  double** d_times = nullptr;  // per field: device pointer to its timestamps
+  double* d_tref = nullptr;    // per field
+  double* d_grid = nullptr;    // per field: vx0, dvx, vy0, dvy
   double* d_sky = nullptr;
   st_candidate* d_hout = nullptr;
   int64_t hout_cap = 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
+  std::string tune_cache;
+  int sms = 0;
   double stack_ms = 0.0;
   int64_t stack_launches = 0;
   int64_t launches = 0;
@@ -125,6 +131,9 @@ void free_plan(st_plan_t* p) {
   cudaFree(p->d_keys);
   cudaFree(p->d_idx);
   cudaFree(p->d_fds);
+  cudaFree(p->d_times);
+  cudaFree(p->d_tref);
+  cudaFree(p->d_grid);
   cudaFree(p->d_sky);
   cudaFree(p->d_hout);
   if (p->e0) cudaEventDestroy(p->e0);
@@ -163,6 +172,52 @@ st_status check_times(const double* t, int N, const st_field& f, int idx) {
 }
 
 size_t store_bytes(int storage) { return storage == ST_F32 ? 4 : 2; }
+
+// Autotuning cache: a flat JSON object {"<field key>": variant, ...}.
+std::string tune_key(const st_field& f, int storage, int sms) {
+  char b[160];
+  snprintf(b, sizeof b, "W%d_H%d_N%d_nvx%d_nvy%d_st%d_sm%d", f.width, f.height, f.n_frames, f.nvx,
+           f.nvy, storage, sms);
+  return b;
+}
+
+int tune_lookup(const std::string& path, const std::string& key) {
+  if (path.empty()) return -1;
+  FILE* fh = fopen(path.c_str(), "r");
+  if (!fh) return -1;
+  std::string txt;
+  char buf[4096];
+  size_t n;
+  while ((n = fread(buf, 1, sizeof buf, fh)) > 0) txt.append(buf, n);
+  fclose(fh);
+  size_t at = txt.find("\"" + key + "\"");
+  if (at == std::string::npos) return -1;
+  at = txt.find(':', at);
+  if (at == std::string::npos) return -1;
+  return atoi(txt.c_str() + at + 1);
+}
+
+void tune_store(const std::string& path, const std::string& key, int variant) {
+  if (path.empty()) return;
+  std::string txt;
+  if (FILE* fh = fopen(path.c_str(), "r")) {
+    char buf[4096];
+    size_t n;
+    while ((n = fread(buf, 1, sizeof buf, fh)) > 0) txt.append(buf, n);
+    fclose(fh);
+  }
+  size_t close = txt.rfind('}');
+  char entry[256];
+  snprintf(entry, sizeof entry, "\"%s\": %d", key.c_str(), variant);
+  if (close == std::string::npos || txt.find('"') == std::string::npos)
+    txt = std::string("{") + entry + "}\n";
+  else
+    txt = txt.substr(0, close) + ", " + entry + "}\n";
+  if (FILE* fh = fopen(path.c_str(), "w")) {
+    fputs(txt.c_str(), fh);
+    fclose(fh);
+  }
+}
 
 // Tables + optional normalisation for field fi with the given frames/times.
 st_status prepare_field(st_plan_t* p, int fi, const float* d_frames, const double* h_times,
@@ -221,14 +276,30 @@ st_status device_search(st_plan_t* p, const float* const* d_frames, const double
   CK(cudaMemcpyAsync(p->d_fds, fds.data(), sizeof(FieldDev) * nf, cudaMemcpyHostToDevice, p->s));
   CK(cudaMemsetAsync(p->d_ctr, 0, sizeof(Counters), p->s));
   std::vector<char> use_fast(nf, 0);
+  bool tuned_now = false;
   for (int fi = 0; fi < nf; ++fi) {
     bool fits = false;
-    if (p->F[fi].fast) {
-      L += fast_prepare(fds[fi], p->F[fi].fast, p->s, &fits);
+    FieldPlan& fp = p->F[fi];
+    if (fp.fast) {
+      L += fast_prepare(fds[fi], fp.fast, p->s, &fits);
       CK(cudaGetLastError());
+      if (fits && p->o.tile == -1 && !fp.tuned) {
+        const std::string key = tune_key(fp.f, fds[fi].storage, p->sms);
+        int v = tune_lookup(p->tune_cache, key);
+        if (v >= 0 && v < fast_num_variants_for(fds[fi].storage)) {
+          fast_set_variant(fp.fast, v);
+        } else {
+          L += fast_autotune(fds[fi], fp.fast, 8ll * p->sms, p->d_pend, p->pend_cap, p->d_ctr,
+                             p->s);
+          tune_store(p->tune_cache, key, fast_get_variant(fp.fast));
+          tuned_now = true;
+        }
+        fp.tuned = true;
+      }
     }
     use_fast[fi] = fits;
   }
+  if (tuned_now) CK(cudaMemsetAsync(p->d_ctr, 0, sizeof(Counters), p->s));
   CK(cudaEventRecord(p->e0, p->s));
   int64_t stack_launches = 0;
   for (int fi = 0; fi < nf; ++fi) {
@@ -319,6 +390,9 @@ st_status st_plan(const st_field* fields, int32_t n_fields, const st_opts* opts,
     return e == cudaSuccess;
   };
   guard(cudaGetDevice(&p->device), "cudaGetDevice");
+  guard(cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device),
+        "cudaDeviceGetAttribute");
+  if (opts->tune_cache) p->tune_cache = opts->tune_cache;
   p->F.resize(n_fields);
   int maxN = 0;
   for (int i = 0; i < n_fields && st == ST_OK; ++i) {
@@ -364,6 +438,27 @@ st_status st_plan(const st_field* fields, int32_t n_fields, const st_opts* opts,
     guard(cudaMalloc(&p->d_ctr, sizeof(Counters)), "cudaMalloc(counters)");
     guard(cudaMallocHost(&p->h_ctr, sizeof(Counters)), "cudaMallocHost(counters)");
     guard(cudaMalloc(&p->d_fds, sizeof(FieldDev) * n_fields), "cudaMalloc(fields)");
+    guard(cudaMalloc(&p->d_times, sizeof(double*) * n_fields), "cudaMalloc(times)");
+    guard(cudaMalloc(&p->d_tref, sizeof(double) * n_fields), "cudaMalloc(tref)");
+    guard(cudaMalloc(&p->d_grid, sizeof(double) * 4 * n_fields), "cudaMalloc(grid)");
+    if (st == ST_OK) {
+      std::vector<double*> tp(n_fields);
+      std::vector<double> tr(n_fields), gr(4 * n_fields);
+      for (int i = 0; i < n_fields; ++i) {
+        tp[i] = p->F[i].d_t;
+        tr[i] = p->F[i].f.t_ref;
+        gr[4 * i] = p->F[i].f.vx0;
+        gr[4 * i + 1] = p->F[i].f.dvx;
+        gr[4 * i + 2] = p->F[i].f.vy0;
+        gr[4 * i + 3] = p->F[i].f.dvy;
+      }
+      guard(cudaMemcpy(p->d_times, tp.data(), sizeof(double*) * n_fields, cudaMemcpyHostToDevice),
+            "cudaMemcpy(times)");
+      guard(cudaMemcpy(p->d_tref, tr.data(), sizeof(double) * n_fields, cudaMemcpyHostToDevice),
+            "cudaMemcpy(tref)");
+      guard(cudaMemcpy(p->d_grid, gr.data(), sizeof(double) * 4 * n_fields, cudaMemcpyHostToDevice),
+            "cudaMemcpy(grid)");
+    }
     guard(cudaMalloc(&p->d_sky, sizeof(double) * sky_partial_doubles(maxN)), "cudaMalloc(sky)");
     guard(cudaEventCreate(&p->e0), "cudaEventCreate");
     guard(cudaEventCreate(&p->e1), "cudaEventCreate");
@@ -515,14 +610,42 @@ st_status st_last_stack_kernel_time(const st_plan_t* p, double* ms, int64_t* lau
   return ST_OK;
 }
 
-st_status st_refine(st_plan_t*, const st_candidate*, int64_t, int32_t, int32_t, float, float, float,
-                    st_refined*, float*) {
-  return fail(ST_ERR_UNSUPPORTED, "st_refine: not built yet");
+st_status st_refine(st_plan_t* p, const st_candidate* d_in, int64_t n, int32_t steps,
+                    int32_t optimizer, float fwhm, float lr_pos, float lr_vel, st_refined* d_out,
+                    float* d_grad_out) {
+  if (!p) return fail(ST_ERR_INVALID, "plan is NULL");
+  if (n < 0 || (n > 0 && (!d_in || !d_out)) || steps < 0 || steps > 100000)
+    return fail(ST_ERR_INVALID, "n >= 0, d_in/d_out non-NULL, 0 <= steps <= 100000");
+  if (!(fwhm > 0.0f) || !std::isfinite(fwhm) || !std::isfinite(lr_pos) || !std::isfinite(lr_vel))
+    return fail(ST_ERR_INVALID, "fwhm > 0 and finite learning rates required");
+  if (optimizer != 0) return fail(ST_ERR_UNSUPPORTED, "only optimizer 0 (Adam) is built");
+  if (!p->has_search) return fail(ST_ERR_INVALID, "st_refine needs a prior st_stack_search");
+  if (n == 0) return ST_OK;
+  int storage = (p->F[0].d_cube ? p->o.storage : ST_F32);
+  launch_refine(p->d_fds, p->d_times, p->d_tref, p->d_grid, storage, true, nullptr, nullptr,
+                nullptr, d_in, n, steps, fwhm, lr_pos, lr_vel, nullptr, nullptr, d_grad_out,
+                d_out, p->s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(p->s));
+  p->launches = 1;
+  return ST_OK;
 }
 
-st_status st_refine_eval(st_plan_t*, const float*, const int32_t*, const int32_t*, int64_t, float,
-                         float*, float*, float*) {
-  return fail(ST_ERR_UNSUPPORTED, "st_refine_eval: not built yet");
+st_status st_refine_eval(st_plan_t* p, const float* d_theta, const int32_t* d_centre,
+                         const int32_t* d_field, int64_t n, float fwhm, float* d_J, float* d_snr,
+                         float* d_grad) {
+  if (!p) return fail(ST_ERR_INVALID, "plan is NULL");
+  if (n < 0 || (n > 0 && (!d_theta || !d_centre || !d_field || !d_J || !d_snr)))
+    return fail(ST_ERR_INVALID, "n >= 0 and theta, centre, field, J, snr non-NULL");
+  if (!(fwhm > 0.0f) || !std::isfinite(fwhm)) return fail(ST_ERR_INVALID, "fwhm must be > 0");
+  if (!p->has_search) return fail(ST_ERR_INVALID, "st_refine_eval needs a prior st_stack_search");
+  if (n == 0) return ST_OK;
+  int storage = (p->F[0].d_cube ? p->o.storage : ST_F32);
+  launch_refine(p->d_fds, p->d_times, p->d_tref, p->d_grid, storage, false, d_theta, d_centre,
+                d_field, nullptr, n, 0, fwhm, 0.0f, 0.0f, d_J, d_snr, d_grad, nullptr, p->s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(p->s));
+  return ST_OK;
 }
 
 }  // extern "C"

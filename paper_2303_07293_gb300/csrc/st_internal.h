@@ -77,6 +77,10 @@ int launch_stack_generic(const FieldDev& fd, int mode, int k0, int nk, const int
 struct FastPlan;
 int fast_plan_size_bytes();
 int fast_num_variants();
+int fast_num_variants_for(int storage);
+int fast_get_variant(const FastPlan* fp);
+int fast_autotune(const FieldDev& fd, FastPlan* fp, int64_t items, Pending* pend,
+                  int64_t pend_cap, Counters* ctr, cudaStream_t s);
 const char* fast_variant_name(int v);
 void fast_set_variant(FastPlan* fp, int v);
 // Whether the field can use the fast kernel at all (nearest, FP32 storage,
@@ -105,5 +109,15 @@ int launch_sort_gather(uint64_t* keys, uint32_t* idx, int64_t n_pow2, const Coun
                        cudaStream_t s);
 int launch_pad_keys(uint64_t* keys, uint32_t* idx, int64_t n_pow2, const Counters* ctr,
                     cudaStream_t s);
+
+// Refinement: optimise == false evaluates J, SNR and (optionally) dJ/dtheta at
+// the given theta; optimise == true runs `steps` Adam steps from each
+// candidate's grid velocity and pixel, with F at its optimum, and writes the
+// refined records.
+int launch_refine(const FieldDev* fds, const double* const* times, const double* t_ref,
+                  const double* grid, int storage, bool optimise, const float* theta,
+                  const int32_t* centre, const int32_t* field, const st_candidate* cand,
+                  int64_t n, int steps, float fwhm, float lr_pos, float lr_vel, float* J,
+                  float* snr, float* grad, st_refined* out, cudaStream_t s);
 
 }  // namespace st

@@ -93,6 +93,26 @@ def test_fast_dense_candidates_every_row(st):
         assert np.array_equal(got["stack"], ref["stack"].astype(np.float32)), tile
 
 
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_fast_reduced_storage_bitexact_on_rounded_frames(st, storage):
+    fr, t, f = field(13, W=104, H=70, N=33, nvx=17, nvy=10)
+    f = dict(f, snr_threshold=2.5)
+    rounded = fr.astype(np.float16).astype(np.float32) if storage == "f16" else \
+        oracle.round_bf16(fr)
+    ks = np.arange(f["nvx"] * f["nvy"], dtype=np.int32)
+    oS, oC = oracle.stack_planes(rounded, t, f, ks, prec="fp32")
+    ref = oracle.search(rounded, t, f, prec="fp32")
+    for tile in (0, 2, 3):
+        with st.Plan(f, storage=storage, tile=tile) as p:
+            S, Cv = p.dump_stack(0, dev(fr), t, ks)
+            got = p.candidates(dev(fr), t)
+            assert p.last_stack_variant(0) == 1
+        assert np.array_equal(S.cpu().numpy(), oS.astype(np.float32)), tile
+        assert np.array_equal(Cv.cpu().numpy(), oC), tile
+        assert got[["x", "y", "k", "n_cov"]].tolist() == \
+            ref[["x", "y", "k", "n_cov"]].tolist(), tile
+
+
 def test_fast_with_normalised_cube(st):
     d = synth.make_field("mid", width=192, n_frames=24, nv=33, n_movers=5)
     raw = d["frames"] * 1.5 + 40.0
@@ -126,3 +146,42 @@ def test_add_rate_probe(st):
     for var in (0, 1, 2):
         per_clk, t = st.probe_add_rate(var, 4000)
         assert 16 <= per_clk <= 1024 and t > 1.0, (var, per_clk, t)
+
+
+def test_autotune_picks_a_variant_and_caches_it(st, tmp_path):
+    fr, t, f = field(14, W=128, H=96, N=40, nvx=16, nvy=12)
+    cache = str(tmp_path / "tune.json")
+    with st.Plan(f) as p:
+        ref = p.candidates(dev(fr), t)
+    with st.Plan(f, tile=-1, tune_cache=cache) as p:
+        got = p.candidates(dev(fr), t)
+        assert p.last_stack_variant(0) == 1
+    assert got.tobytes() == ref.tobytes()
+    import json
+    with open(cache) as fh:
+        tab = json.load(fh)
+    assert len(tab) == 1 and 0 <= list(tab.values())[0] < 8
+    with st.Plan(f, tile=-1, tune_cache=cache) as p:   # served from the cache
+        again = p.candidates(dev(fr), t)
+    assert again.tobytes() == ref.tobytes()
+
+
+def test_multi_field_plan_equals_single_field_plans(st):
+    specs = [dict(seed=15, W=96, H=64, N=20, nvx=9, nvy=8),
+             dict(seed=16, W=128, H=48, N=33, nvx=12, nvy=5),
+             dict(seed=17, W=64, H=64, N=9, nvx=8, nvy=8)]
+    fields = [field(**sp) for sp in specs]
+    singles = []
+    for fr, t, f in fields:
+        with st.Plan(f) as p:
+            singles.append(p.candidates(dev(fr), t))
+    with st.Plan([f for _, _, f in fields]) as p:
+        out, n, status = p.search([dev(fr) for fr, _, _ in fields], [t for _, t, _ in fields],
+                                  capacity=1 << 16)
+        allc = p.to_numpy(out, n)
+    assert status == st.ST_OK
+    for i, c in enumerate(singles):
+        mine = allc[allc["field"] == i]
+        assert mine[["x", "y", "k", "n_cov"]].tolist() == c[["x", "y", "k", "n_cov"]].tolist()
+        assert np.array_equal(mine["stack"], c["stack"])
+    assert np.all(np.diff(allc["field"]) >= 0)   # sorted by field first
