@@ -74,6 +74,7 @@ struct Store<__nv_bfloat16> {
 };
 constexpr int kSuper = 4;        // pixel tiles per super-tile side (L2 locality)
 constexpr uint64_t kWaitNs = 2000000000ull;  // wait limit: 2 s of wall-clock time
+constexpr unsigned kProducerSleepNs = 128;  // producer back-off between polls
 constexpr int kParamBytes = 28672;  // staircase pattern ids carried in the kernel parameters
 constexpr int kPatterns = 15;
 
@@ -303,7 +304,7 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
   constexpr int kOut = kMB * KY;  // outputs per thread per item
   constexpr int kItemSlots = 8;
   constexpr int kNoop = kPatterns;  // pattern id of a padding frame
-  static_assert(F <= 32, "one producer lane per frame of a stage");
+  static_assert(F <= 4, "pattern ids of a stage are packed into one word");
   extern __shared__ __align__(128) float smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[S];
   __shared__ __align__(8) uint64_t empty_bar[S];
@@ -314,7 +315,8 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
                                  ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t box_bytes = (uint32_t)kBoxH * kBoxW * sizeof(T);
-  const int box_floats = p.stage_floats;  // one frame's box in elements, 128-byte aligned
+  // one frame's box in elements, padded to 128 bytes (compile-time stride)
+  constexpr int box_floats = ((kBoxH * kBoxW * (int)sizeof(T) + 127) & ~127) / (int)sizeof(T);
   const int N = p.N;
   const int spi = (N + F - 1) / F;       // stages per item
   const int G = (int)gridDim.x;
@@ -338,7 +340,8 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
     int slot = 0, item = 0, st = 0;
     Item it = decode_item(p, blockIdx.x);
     for (int seq = 0; seq < n_stages; ++seq) {
-      if (seq >= S && !mbar_wait(&empty_bar[slot], (uint32_t)(seq / S - 1) & 1u, kWaitNs)) {
+      if (seq >= S && !mbar_wait_sleep(&empty_bar[slot], (uint32_t)(seq / S - 1) & 1u, kWaitNs,
+                                        kProducerSleepNs)) {
         if (lane == 0) atomicOr(&p.ctr->error, ERR_TIMEOUT);
         break;  // consumers time out on the missing stage (bounded)
       }
@@ -381,8 +384,10 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
   uint32_t c_ph = 0;
   bool ok = true;
   for (int item = 0; item < my_items && ok; ++item) {
-    // uniform; only the pattern row stays live through the frame loop
-    const unsigned char* pat = p.pat + decode_item(p, blockIdx.x + (int64_t)item * G).g * N;
+    // uniform; only the pattern row stays live through the frame loop.  The
+    // row is padded to spi * F entries with no-op ids.
+    const unsigned char* pat =
+        p.pat + decode_item(p, blockIdx.x + (int64_t)item * G).g * (spi * F);
     float2 acc[kMB][KY / 2];
 #pragma unroll
     for (int j = 0; j < kMB; ++j)
@@ -395,12 +400,22 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
         ok = false;
         break;
       }
+      // the stage's pattern ids: one packed word per stage (F <= 4)
+      uint32_t idw = 0;
+      if constexpr (F == 4) {
+        idw = *reinterpret_cast<const uint32_t*>(pat + st * F);  // rows padded to 4 bytes
+      } else {
+#pragma unroll
+        for (int fi = 0; fi < F; ++fi) idw |= (uint32_t)pat[st * F + fi] << (8 * fi);
+      }
       const T* stage = smem + (size_t)(c_slot * F) * box_floats + lane;
+      uint32_t oc_next = slot_ocol[c_slot * F];
+#pragma unroll 1
       for (int fi = 0; fi < F; ++fi) {
-        const int f = st * F + fi;
-        const int id = f < N ? (int)pat[f] : kNoop;
-        const int ocol = (slot_ocol[c_slot * F + fi] >> (4 * xw)) & 15u;
-        const T* col = stage + fi * box_floats + ocol;
+        const int id = (idw >> (8 * fi)) & 0xffu;
+        const uint32_t oc = oc_next;
+        if (fi + 1 < F) oc_next = slot_ocol[c_slot * F + fi + 1];
+        const T* col = stage + fi * box_floats + ((oc >> (4 * xw)) & 15u);
         float w[KY + 3];
 #pragma unroll
         for (int r = 0; r < KY + 3; ++r) w[r] = Store<T>::f(col[r * kBoxW]);
@@ -424,7 +439,8 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
           case 12: add_pattern<KY, 12>(acc, w); break;
           case 13: add_pattern<KY, 13>(acc, w); break;
           case 14: add_pattern<KY, 14>(acc, w); break;
-          default: break;  // padding frame
+          case kNoop: break;  // padding frame
+          default: __builtin_unreachable();
         }
       }
       if (++c_slot == S) {
@@ -528,7 +544,7 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
 struct Variant {
   void (*fn)(CUtensorMap, FastArgs);
   void (*dump_fn)(CUtensorMap, FastArgs);
-  int threads, stages, ky;
+  int threads, stages, ky, stages_f;
   const char* name;
 };
 
@@ -536,7 +552,7 @@ struct Variant {
   {                                                                                           \
     (void (*)(CUtensorMap, FastArgs))k_stack_fast<T, KY, S, F, false>,                          \
         (void (*)(CUtensorMap, FastArgs))k_stack_fast<T, KY, S, F, true>, 32 * (kXV + 1), S * F,   \
-        KY, #T "_ky" #KY "_s" #S "_f" #F                                                       \
+        KY, F, #T "_ky" #KY "_s" #S "_f" #F                                                    \
   }
 const Variant kVarF32[] = {ST_VARIANT(float, 16, 6, 4), ST_VARIANT(float, 16, 8, 4),
                            ST_VARIANT(float, 20, 6, 4), ST_VARIANT(float, 24, 6, 4),
@@ -828,7 +844,9 @@ int launch_stack_fast(const FieldDev& fd, const FastPlan* cfp, int k0, int nk,
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int G = kParamBytes / fd.N < fp->nB ? kParamBytes / fd.N : fp->nB;
+  const int F_var = var.stages_f;  // frames per stage of the variant
+  const int Np = ((fd.N + F_var - 1) / F_var) * F_var;  // item frames padded to whole stages
+  const int G = kParamBytes / Np < fp->nB ? kParamBytes / Np : fp->nB;
   if (G < 1) return -1;
   int launches = 0;
   for (int B0 = 0; B0 < fp->nB; B0 += G) {
@@ -836,7 +854,9 @@ int launch_stack_fast(const FieldDev& fd, const FastPlan* cfp, int k0, int nk,
     a.B0 = B0;
     a.G = fp->nB - B0 < G ? fp->nB - B0 : G;
     for (int g = 0; g < a.G; ++g)
-      for (int i = 0; i < fd.N; ++i) a.pat[g * fd.N + i] = fp->h_pat[(size_t)i * fp->nB + B0 + g];
+      for (int i = 0; i < Np; ++i)
+        a.pat[g * Np + i] =
+            i < fd.N ? fp->h_pat[(size_t)i * fp->nB + B0 + g] : (unsigned char)kPatterns;
     a.n_items = (int64_t)a.super_x * a.super_y * kSuper * kSuper * a.nA * a.G;
     if (fp->item_limit > 0 && a.n_items > fp->item_limit) a.n_items = fp->item_limit;
     const int per_sm = ky <= 16 ? 2 : 1;  // persistent CTAs per SM

@@ -83,6 +83,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64
   }
 }
 
+// As mbar_wait, but sleeps sleep_ns between polls: for a warp that runs far
+// ahead of its consumers (a TMA producer), so that its polling does not take
+// issue slots from the warps that share its scheduler.
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity,
+                                                uint64_t limit_ns, unsigned sleep_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    __nanosleep(sleep_ns);
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+}
+
 // 3-D tiled TMA load of one box into shared memory, completing on `bar`.
 // x must be a multiple of 16 bytes / element size (checked by the caller's
 // table construction); y, z may be negative or past the end (zero fill).
