@@ -1,34 +1,37 @@
 // k_stack_fast.cu — register-window shift-and-stack kernel for sm_103a.
 //
-// Computes the same nearest-pixel stack as the generic kernel (Sec. 1 /
-// Sec. 2.1: every frame shifted by the rounded trial motion v*(t_i - t_ref)
-// and summed in frame order with one FP32 accumulator per output), laid out
-// for the GB300 FP32 pipe:
+// Computes the same stack as the generic kernel (Sec. 1 / Sec. 2.1: every
+// frame shifted by the trial motion v*(t_i - t_ref) and summed in frame
+// order with one FP32 accumulator per output), laid out for the GB300 FP32
+// pipe, for nearest-pixel and bilinear sampling:
 //
-// * A block owns a 32 x 32 pixel tile and a velocity tile of 8 x-velocities
-//   (one per warp) times 4 y-velocities (shared by all warps).  Lane l owns
-//   column X0 + l; each thread accumulates the 32 rows of its column for its
-//   warp's x-velocity and the 4 y-velocities: 128 FP32 accumulators.
-// * Per frame, one elected thread issues a TMA tile load of the block's
-//   footprint (40 x 35 FP32, zero-filled outside the frame) into a ring of
-//   shared-memory stages guarded by mbarriers (full: bytes landed; empty: all
-//   warps done).  Every wait is bounded.
+// * A block owns a 32 x KY pixel tile and a velocity tile of 8 x-velocities
+//   (one per consumer warp) times 4 y-velocities (shared by all warps).  Lane
+//   l owns column X0 + l; each thread accumulates the KY rows of its column
+//   for its warp's x-velocity and the 4 y-velocities.
+// * Per frame, a producer warp issues a TMA tile load of the block's
+//   footprint (zero-filled outside the frame) into a ring of shared-memory
+//   stages guarded by mbarriers (full: bytes landed; empty: all warps done).
+//   Every wait is bounded.
 // * A warp's x-shift is only an address: lane l reads column l + o_w, so the
 //   32 lanes read 32 consecutive words (no bank conflicts, any alignment).
-// * Each thread loads a 35-row window of its column and reuses every value
-//   for the 4 y-velocities: y-velocity j adds window[r + c_j] to row r.  The
-//   row offsets c_j form a monotone staircase with steps of 0 or 1 (15
-//   patterns); the pattern is the same for the whole block in a frame and
+// * Each thread loads a window of its column (KY + 3 rows; bilinear: KY + 4
+//   rows of the column and its right neighbour) and reuses every value for
+//   the 4 y-velocities: y-velocity j reads window row r + c_j for output row
+//   r.  The row offsets c_j form a monotone staircase with steps of 0 or 1
+//   (15 patterns); the pattern is the same for the whole block in a frame and
 //   comes from the kernel parameters, so one uniform switch per frame picks a
-//   straight-line body.  Even offsets use paired adds (add.f32x2) on row
-//   pairs, odd offsets scalar adds; both cost the same FMA-pipe cycles.
+//   straight-line body.  Nearest: even offsets use paired adds (add.f32x2) on
+//   row pairs, odd offsets scalar adds.  Bilinear: four fused multiply-adds
+//   per sample with the weights of the warp's x-fraction and the y-velocity's
+//   y-fraction, in the generic kernel's order.
 // * After the last frame, outputs are compared with the block's lowest
-//   possible threshold; the rare survivors get their exact coverage and go
-//   to the warp-aggregated pending list for the local-maximum test.
+//   possible threshold; the rare survivors go to the warp-aggregated pending
+//   list, where the resolver forms their exact coverage and local maximum.
 //
-// The sums are the same FP32 additions in the same order as the generic
-// kernel (out-of-frame samples add +0.0 from the TMA zero fill, which leaves
-// any sum unchanged), so the two kernels agree bit for bit.
+// The sums are the same FP32 operations in the same order as the generic
+// kernel (out-of-frame taps read +0.0 from the TMA zero fill, as the generic
+// kernel's taps do), so the two kernels agree bit for bit.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -41,6 +44,7 @@
 
 #include "st_internal.h"
 #include "st_pending.cuh"
+#include "st_sample.cuh"
 #include "st_tma.cuh"
 
 namespace st {
@@ -93,6 +97,10 @@ struct FastArgs {
   const int* ymax;  // [nB]
   const int32_t* sx;
   const int32_t* sy;
+  const float* fx;   // bilinear: FP32 fractions [N][nvx], [N][nvy]
+  const float* fy;
+  const float4* fxt;  // bilinear: [N][nA][2] x-fractions of a velocity tile's 8 x-velocities
+  const float4* fyt;  // bilinear: [N][nB] y-fractions of its 4 y-velocities
   const float* thr;
   // coverage prefix tables: for velocity a, covx[a * cov_len + s - cov_xmin[a]]
   // = number of frames with sx(i, a) <= s (likewise y)
@@ -245,6 +253,32 @@ __device__ __forceinline__ void add_pattern(float2 (&acc)[kMB][KY / 2], const fl
   add_column<KY, pat_off(ID, 3)>(acc[3], w, std::make_integer_sequence<int, KY / 2>{});
 }
 
+// Bilinear: for the 4 y-velocities, acc[j][row] gets one sample per output
+// row, as four fused multiply-adds in the generic kernel's order
+// (bilinear_acc), with taps from the window rows r + c_j and r + c_j + 1 of
+// the column (c0) and its right neighbour (c1).
+template <int KY, int J, int C>
+__device__ __forceinline__ void add_bl_column(float2 (&acc)[KY / 2], const BW& w,
+                                              const float (&c0)[KY + 4],
+                                              const float (&c1)[KY + 4]) {
+#pragma unroll
+  for (int m = 0; m < KY / 2; ++m) {
+    const int r = 2 * m + C;
+    acc[m].x = bilinear_acc(acc[m].x, w, c0[r], c1[r], c0[r + 1], c1[r + 1]);
+    acc[m].y = bilinear_acc(acc[m].y, w, c0[r + 1], c1[r + 1], c0[r + 2], c1[r + 2]);
+  }
+}
+
+template <int KY, int ID>
+__device__ __forceinline__ void add_pattern_bl(float2 (&acc)[kMB][KY / 2], const BW (&w)[kMB],
+                                               const float (&c0)[KY + 4],
+                                               const float (&c1)[KY + 4]) {
+  add_bl_column<KY, 0, pat_off(ID, 0)>(acc[0], w[0], c0, c1);
+  add_bl_column<KY, 1, pat_off(ID, 1)>(acc[1], w[1], c0, c1);
+  add_bl_column<KY, 2, pat_off(ID, 2)>(acc[2], w[2], c0, c1);
+  add_bl_column<KY, 3, pat_off(ID, 3)>(acc[3], w[3], c0, c1);
+}
+
 // Number of frames whose shift s satisfies lo <= s <= hi, from a prefix table.
 __device__ __forceinline__ int count_shifts(const int* pre, int smin, int smax, int N, int lo,
                                             int hi) {
@@ -258,6 +292,17 @@ __device__ int exact_coverage(const FastArgs& p, int x, int y, int av, int bv) {
     int u = x + __ldg(p.sx + (int64_t)i * p.nvx + av);
     int w = y + __ldg(p.sy + (int64_t)i * p.nvy + bv);
     c += (u >= 0 && u < p.W && w >= 0 && w < p.H);
+  }
+  return c;
+}
+
+__device__ int exact_coverage_bl(const FastArgs& p, int x, int y, int av, int bv) {
+  int c = 0;
+  for (int i = 0; i < p.N; ++i) {
+    int u = x + __ldg(p.sx + (int64_t)i * p.nvx + av);
+    int w = y + __ldg(p.sy + (int64_t)i * p.nvy + bv);
+    c += bilinear_inside(u, __ldg(p.fx + (int64_t)i * p.nvx + av), p.W) &&
+         bilinear_inside(w, __ldg(p.fy + (int64_t)i * p.nvy + bv), p.H);
   }
   return c;
 }
@@ -284,7 +329,7 @@ __device__ __forceinline__ Item decode_item(const FastArgs& p, int64_t L) {
   return it;
 }
 
-// Persistent kernel: every CTA walks the items blockIdx.x, blockIdx.x +
+// Persistent kernel (BL: bilinear sampling): every CTA walks the items blockIdx.x, blockIdx.x +
 // gridDim.x, ...  Each item's frames are padded to whole stages of F frames
 // (padding frames are no-ops with no copy).  Warp 8 is the producer: it runs
 // ahead in stages, its lanes fetch the per-frame table entries and issue the
@@ -294,12 +339,13 @@ __device__ __forceinline__ Item decode_item(const FastArgs& p, int64_t L) {
 // parameters through a warp-uniform index, so its switch is a uniform
 // branch.  A ring of S stages runs continuously across items.  Every wait is
 // bounded in time.
-template <typename T, int KY, int S, int F, bool DUMP>
+template <typename T, int KY, int S, int F, bool DUMP, bool BL>
 __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
     k_stack_fast(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ FastArgs p) {
   constexpr int kBoxW = Store<T>::kBoxW;
   constexpr int kTY = KY;         // tile height: one row group of KY rows per thread
-  constexpr int kBoxH = KY + 3;   // tile rows + largest staircase offset
+  constexpr int kBoxH = KY + 3 + (BL ? 1 : 0);  // tile rows + staircase offset (+ lower tap)
+  constexpr int kEdge = BL ? 1 : 0;  // a bilinear sample also reads the next column / row
   constexpr int kCW = kXV;        // consumer warps
   constexpr int kOut = kMB * KY;  // outputs per thread per item
   constexpr int kItemSlots = 8;
@@ -309,6 +355,8 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
   __shared__ __align__(8) uint64_t full_bar[S];
   __shared__ __align__(8) uint64_t empty_bar[S];
   __shared__ uint32_t slot_ocol[S * F];     // packed 4-bit column offsets of the 8 warps
+  __shared__ float slot_fx[BL ? S * F * kXV : 1];  // bilinear: x-fraction of each warp
+  __shared__ float4 slot_fy[BL ? S * F : 1];       // bilinear: y-fractions of the 4 y-velocities
   __shared__ int item_inside[kItemSlots];   // frames of an item fully inside the frame
 
   T* smem = reinterpret_cast<T*>(reinterpret_cast<char*>(smem_raw) +
@@ -352,8 +400,18 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
         const int4 xe = __ldg(p.xt + (int64_t)fr * p.nA + it.A);
         const int4 ye = __ldg(p.yt + (int64_t)fr * p.nB + it.B);
         slot_ocol[slot * F + lane] = (uint32_t)xe.y;
-        const bool inside = it.X0 + xe.z >= 0 && it.X0 + kTX - 1 + xe.w < p.W &&
-                            it.Y0 + ye.x >= 0 && it.Y0 + kTY - 1 + ye.y < p.H;
+        if constexpr (BL) {
+          const float4 f0 = __ldg(p.fxt + 2 * ((int64_t)fr * p.nA + it.A));
+          const float4 f1 = __ldg(p.fxt + 2 * ((int64_t)fr * p.nA + it.A) + 1);
+          float* d = slot_fx + (slot * F + lane) * kXV;
+          d[0] = f0.x; d[1] = f0.y; d[2] = f0.z; d[3] = f0.w;
+          d[4] = f1.x; d[5] = f1.y; d[6] = f1.z; d[7] = f1.w;
+          slot_fy[slot * F + lane] = __ldg(p.fyt + (int64_t)fr * p.nB + it.B);
+        }
+        // every sample of the item strictly inside (bilinear: with its right
+        // and lower taps), so every output of the item is covered by frame fr
+        const bool inside = it.X0 + xe.z >= 0 && it.X0 + kTX - 1 + xe.w + kEdge < p.W &&
+                            it.Y0 + ye.x >= 0 && it.Y0 + kTY - 1 + ye.y + kEdge < p.H;
         if (inside) atomicAdd(&item_inside[item % kItemSlots], 1);
         tma_load_3d(smem + (size_t)(slot * F + lane) * box_floats, &tmap, it.X0 + xe.x,
                     it.Y0 + ye.x, fr, &full_bar[slot]);
@@ -416,6 +474,41 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
         const uint32_t oc = oc_next;
         if (fi + 1 < F) oc_next = slot_ocol[c_slot * F + fi + 1];
         const T* col = stage + fi * box_floats + ((oc >> (4 * xw)) & 15u);
+        if constexpr (BL) {
+          float c0[KY + 4], c1[KY + 4];
+#pragma unroll
+          for (int r = 0; r < KY + 4; ++r) {
+            c0[r] = Store<T>::f(col[r * kBoxW]);
+            c1[r] = Store<T>::f(col[r * kBoxW + 1]);
+          }
+          const float fxw = slot_fx[(c_slot * F + fi) * kXV + xw];
+          const float4 fy4 = slot_fy[c_slot * F + fi];
+          if (fi == F - 1) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty_bar[c_slot]);
+          }
+          const BW wt[kMB] = {bilinear_weights(fxw, fy4.x), bilinear_weights(fxw, fy4.y),
+                              bilinear_weights(fxw, fy4.z), bilinear_weights(fxw, fy4.w)};
+          switch (id) {
+            case 0: add_pattern_bl<KY, 0>(acc, wt, c0, c1); break;
+            case 1: add_pattern_bl<KY, 1>(acc, wt, c0, c1); break;
+            case 2: add_pattern_bl<KY, 2>(acc, wt, c0, c1); break;
+            case 3: add_pattern_bl<KY, 3>(acc, wt, c0, c1); break;
+            case 4: add_pattern_bl<KY, 4>(acc, wt, c0, c1); break;
+            case 5: add_pattern_bl<KY, 5>(acc, wt, c0, c1); break;
+            case 6: add_pattern_bl<KY, 6>(acc, wt, c0, c1); break;
+            case 7: add_pattern_bl<KY, 7>(acc, wt, c0, c1); break;
+            case 8: add_pattern_bl<KY, 8>(acc, wt, c0, c1); break;
+            case 9: add_pattern_bl<KY, 9>(acc, wt, c0, c1); break;
+            case 10: add_pattern_bl<KY, 10>(acc, wt, c0, c1); break;
+            case 11: add_pattern_bl<KY, 11>(acc, wt, c0, c1); break;
+            case 12: add_pattern_bl<KY, 12>(acc, wt, c0, c1); break;
+            case 13: add_pattern_bl<KY, 13>(acc, wt, c0, c1); break;
+            case 14: add_pattern_bl<KY, 14>(acc, wt, c0, c1); break;
+            case kNoop: break;  // padding frame
+            default: __builtin_unreachable();
+          }
+        } else {
         float w[KY + 3];
 #pragma unroll
         for (int r = 0; r < KY + 3; ++r) w[r] = Store<T>::f(col[r * kBoxW]);
@@ -441,6 +534,7 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
           case 14: add_pattern<KY, 14>(acc, w); break;
           case kNoop: break;  // padding frame
           default: __builtin_unreachable();
+        }
         }
       }
       if (++c_slot == S) {
@@ -468,7 +562,9 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
               const int64_t o =
                   ((int64_t)bv * p.nvx + av) * p.W * (int64_t)p.H + (int64_t)y * p.W + x;
               p.dump_S[o] = h == 0 ? acc[j][m].x : acc[j][m].y;
-              if (p.dump_C) p.dump_C[o] = exact_coverage(p, x, y, av, bv);
+              if (p.dump_C)
+                p.dump_C[o] = BL ? exact_coverage_bl(p, x, y, av, bv)
+                                 : exact_coverage(p, x, y, av, bv);
             }
           }
     } else {
@@ -492,19 +588,21 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
           }
       } else {
         // edge item: n_cov >= nx + ny - N, with nx / ny the frames whose x / y
-        // sample is inside (ny taken at the item's least covered row), and
+        // sample is inside (bilinear: with its right / lower tap, which
+        // implies inside for any fraction; ny taken at the item's least
+        // covered row), and
         // n_cov >= n_full; thresholds grow with n_cov, so this never drops a
         // candidate
         const int avc = min(av, p.nvx - 1);
         const int nx = count_shifts(p.covx + (int64_t)avc * p.cov_len, __ldg(p.cov_xmin + avc),
-                                    __ldg(p.cov_xmax + avc), N, -x, p.W - 1 - x);
+                                    __ldg(p.cov_xmax + avc), N, -x, p.W - 1 - kEdge - x);
 #pragma unroll
         for (int j = 0; j < kMB; ++j) {
           // ny minimised over the item's rows (lane l takes row l % KY)
           const int bvc = min(it.B * kMB + j, p.nvy - 1);
           const int y = it.Y0 + lane % KY;
           int ny = count_shifts(p.covy + (int64_t)bvc * p.cov_len, __ldg(p.cov_ymin + bvc),
-                                __ldg(p.cov_ymax + bvc), N, -y, p.H - 1 - y);
+                                __ldg(p.cov_ymax + bvc), N, -y, p.H - 1 - kEdge - y);
 #pragma unroll
           for (int d = 16; d > 0; d >>= 1) ny = min(ny, __shfl_xor_sync(0xffffffffu, ny, d));
           const int nlo = max(max(n_full, p.nmin), nx + ny - N);
@@ -548,32 +646,61 @@ struct Variant {
   const char* name;
 };
 
-#define ST_VARIANT(T, KY, S, F)                                                               \
+#define ST_VARIANT(T, KY, S, F, BL)                                                           \
   {                                                                                           \
-    (void (*)(CUtensorMap, FastArgs))k_stack_fast<T, KY, S, F, false>,                          \
-        (void (*)(CUtensorMap, FastArgs))k_stack_fast<T, KY, S, F, true>, 32 * (kXV + 1), S * F,   \
-        KY, F, #T "_ky" #KY "_s" #S "_f" #F                                                    \
+    (void (*)(CUtensorMap, FastArgs))k_stack_fast<T, KY, S, F, false, BL>,                      \
+        (void (*)(CUtensorMap, FastArgs))k_stack_fast<T, KY, S, F, true, BL>, 32 * (kXV + 1),  \
+        S * F, KY, F, #T "_ky" #KY "_s" #S "_f" #F                                             \
   }
-const Variant kVarF32[] = {ST_VARIANT(float, 16, 6, 4), ST_VARIANT(float, 16, 8, 4),
-                           ST_VARIANT(float, 20, 6, 4), ST_VARIANT(float, 24, 6, 4),
-                           ST_VARIANT(float, 16, 12, 2)};
-const Variant kVarF16[] = {ST_VARIANT(__half, 16, 6, 4), ST_VARIANT(__half, 16, 8, 4)};
-const Variant kVarBF16[] = {ST_VARIANT(__nv_bfloat16, 16, 6, 4),
-                            ST_VARIANT(__nv_bfloat16, 16, 8, 4)};
+const Variant kVarF32[] = {ST_VARIANT(float, 16, 6, 4, false), ST_VARIANT(float, 16, 8, 4, false),
+                           ST_VARIANT(float, 20, 6, 4, false), ST_VARIANT(float, 24, 6, 4, false),
+                           ST_VARIANT(float, 16, 12, 2, false)};
+const Variant kVarF16[] = {ST_VARIANT(__half, 16, 6, 4, false),
+                           ST_VARIANT(__half, 16, 8, 4, false)};
+const Variant kVarBF16[] = {ST_VARIANT(__nv_bfloat16, 16, 6, 4, false),
+                            ST_VARIANT(__nv_bfloat16, 16, 8, 4, false)};
+// bilinear sampling: two window columns and 4 weights per y-velocity
+const Variant kVarBlF32[] = {ST_VARIANT(float, 8, 8, 4, true), ST_VARIANT(float, 10, 8, 4, true),
+                             ST_VARIANT(float, 8, 12, 4, true)};
+const Variant kVarBlF16[] = {ST_VARIANT(__half, 8, 8, 4, true)};
+const Variant kVarBlBF16[] = {ST_VARIANT(__nv_bfloat16, 8, 8, 4, true)};
 #undef ST_VARIANT
 constexpr int kNumVariants = sizeof(kVarF32) / sizeof(kVarF32[0]);  // the largest list
 
-const Variant* variants_for(int storage, int* count) {
-  if (storage == ST_F16) {
-    *count = sizeof(kVarF16) / sizeof(kVarF16[0]);
-    return kVarF16;
+#define ST_LIST(L)                            \
+  {                                           \
+    *count = (int)(sizeof(L) / sizeof(L[0])); \
+    return L;                                 \
   }
-  if (storage == ST_BF16) {
-    *count = sizeof(kVarBF16) / sizeof(kVarBF16[0]);
-    return kVarBF16;
+const Variant* variants_for(int storage, bool bl, int* count) {
+  if (bl) {
+    if (storage == ST_F16) ST_LIST(kVarBlF16);
+    if (storage == ST_BF16) ST_LIST(kVarBlBF16);
+    ST_LIST(kVarBlF32);
   }
-  *count = kNumVariants;
-  return kVarF32;
+  if (storage == ST_F16) ST_LIST(kVarF16);
+  if (storage == ST_BF16) ST_LIST(kVarBF16);
+  ST_LIST(kVarF32);
+}
+#undef ST_LIST
+
+// Fractions of a velocity tile, gathered per frame: fxt[(i nA + A) 8 + w] =
+// fx(i, 8A + w) and fyt[(i nB + B) 4 + j] = fy(i, 4B + j) (clamped to the grid).
+__global__ void k_frac_tables(const float* __restrict__ fx, const float* __restrict__ fy, int N,
+                              int nvx, int nvy, int nA, int nB, float* __restrict__ fxt,
+                              float* __restrict__ fyt) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t nX = (int64_t)N * nA * kXV, nY = (int64_t)N * nB * kMB;
+  if (idx < nX) {
+    int64_t i = idx / (nA * kXV);
+    int a = (int)(idx % (nA * kXV));
+    fxt[idx] = fx[i * nvx + min(a, nvx - 1)];
+  } else if (idx < nX + nY) {
+    idx -= nX;
+    int64_t i = idx / (nB * kMB);
+    int b = (int)(idx % (nB * kMB));
+    fyt[idx] = fy[i * nvy + min(b, nvy - 1)];
+  }
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -602,13 +729,16 @@ struct FastPlan {
   CUtensorMap tmap;
   const void* encoded_for = nullptr;
   int encoded_boxh = 0;
-  int variant = 0;         // index into the storage type's variant list
+  int variant = 0;         // index into the (storage type, sampling) variant list
+  bool bl = false;         // bilinear sampling
   int64_t item_limit = 0;  // > 0: run only the first item_limit items (autotuning)
   int nA = 0, nB = 0, N = 0;
   unsigned char* d_pat = nullptr;  // [N][nB] pattern ids
   unsigned char* h_pat = nullptr;  // pinned copy for the kernel parameters
   int4* xt = nullptr;
   int4* yt = nullptr;
+  float* fxt = nullptr;   // bilinear: [N][nA][8] x-fractions
+  float* fyt = nullptr;   // bilinear: [N][nB][4] y-fractions
   int* ranges = nullptr;  // xmin[nA], xmax[nA], ymin[nB], ymax[nB], maxes[2]
   int* h_maxes = nullptr; // pinned
   int* cov = nullptr;     // covx [nvx*len], covy [nvy*len], mins/maxes [2*nvx + 2*nvy]
@@ -620,9 +750,9 @@ int fast_plan_size_bytes() { return (int)sizeof(FastPlan); }
 
 int fast_num_variants() { return kNumVariants; }
 
-int fast_num_variants_for(int storage) {
+int fast_num_variants_for(const FastPlan* fp, int storage) {
   int n = 0;
-  variants_for(storage, &n);
+  variants_for(storage, fp && fp->bl, &n);
   return n;
 }
 
@@ -633,7 +763,7 @@ int fast_get_variant(const FastPlan* fp) { return fp ? fp->variant : -1; }
 int fast_autotune(const FieldDev& fd, FastPlan* fp, int64_t items, Pending* pend,
                   int64_t pend_cap, Counters* ctr, cudaStream_t s) {
   int n = 0;
-  variants_for(fd.storage, &n);
+  variants_for(fd.storage, fp->bl, &n);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -673,19 +803,23 @@ void fast_set_variant(FastPlan* fp, int v) {
 
 bool fast_eligible(const FieldDev& fd, int mode) {
   const int align = fd.storage == ST_F32 ? 4 : 8;  // 16-byte rows for the tensor map
-  return mode == ST_NEAREST && fd.W % align == 0 && encode_fn() != nullptr &&
-         fd.W >= 8 && fd.H >= 1;
+  return (mode == ST_NEAREST || mode == ST_BILINEAR) && fd.W % align == 0 &&
+         encode_fn() != nullptr && fd.W >= 8 && fd.H >= 1;
 }
 
-bool fast_plan_build(const FieldDev& fd, const int32_t*, const int32_t*, FastPlan** out,
-                     cudaStream_t) {
+bool fast_plan_build(const FieldDev& fd, int mode, FastPlan** out) {
   *out = nullptr;
   FastPlan* fp = new (std::nothrow) FastPlan();
   if (!fp) return false;
   fp->nA = (fd.nvx + kXV - 1) / kXV;
   fp->nB = (fd.nvy + kMB - 1) / kMB;
   fp->N = fd.N;
-  bool good = cudaMalloc(&fp->xt, sizeof(int4) * (size_t)fd.N * fp->nA) == cudaSuccess &&
+  fp->bl = mode == ST_BILINEAR;
+  const size_t nfx = fp->bl ? (size_t)fd.N * fp->nA * kXV : 1;
+  const size_t nfy = fp->bl ? (size_t)fd.N * fp->nB * kMB : 1;
+  bool good = cudaMalloc(&fp->fxt, sizeof(float) * nfx) == cudaSuccess &&
+              cudaMalloc(&fp->fyt, sizeof(float) * nfy) == cudaSuccess &&
+              cudaMalloc(&fp->xt, sizeof(int4) * (size_t)fd.N * fp->nA) == cudaSuccess &&
               cudaMalloc(&fp->yt, sizeof(int4) * (size_t)fd.N * fp->nB) == cudaSuccess &&
               cudaMalloc(&fp->ranges, sizeof(int) * (2 * fp->nA + 2 * fp->nB + 3)) == cudaSuccess &&
               cudaMallocHost(&fp->h_maxes, sizeof(int) * 3) == cudaSuccess &&
@@ -703,6 +837,8 @@ void fast_plan_free(FastPlan* fp) {
   if (!fp) return;
   cudaFree(fp->xt);
   cudaFree(fp->yt);
+  cudaFree(fp->fxt);
+  cudaFree(fp->fyt);
   cudaFree(fp->ranges);
   cudaFree(fp->cov);
   if (fp->h_maxes) cudaFreeHost(fp->h_maxes);
@@ -712,7 +848,8 @@ void fast_plan_free(FastPlan* fp) {
 }
 
 // Builds the per-frame tile tables and reports whether the field's motion
-// fits the kernel (column offsets <= 8 within 8 x-velocities, staircase row
+// fits the kernel (column offsets within the box, 8 for FP32 nearest, 7 for
+// FP32 bilinear, 15 for 16-bit storage, among 8 x-velocities; staircase row
 // offsets within 4 y-velocities).  Synchronises s.
 int fast_prepare(const FieldDev& fd, FastPlan* fp, cudaStream_t s, bool* fits) {
   *fits = false;
@@ -732,6 +869,11 @@ int fast_prepare(const FieldDev& fd, FastPlan* fp, cudaStream_t s, bool* fits) {
                                                             nB, fp->xt, fp->yt, xmin, xmax, ymin,
                                                             ymax, maxes, fp->d_pat,
                                                             fd.storage == ST_F32 ? 4 : 8);
+  if (fp->bl) {
+    int64_t nf = (int64_t)fd.N * (nA * kXV + nB * kMB);
+    k_frac_tables<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(fd.fx, fd.fy, fd.N, fd.nvx, fd.nvy,
+                                                               nA, nB, fp->fxt, fp->fyt);
+  }
   k_shift_spread<<<(fd.nvx + 127) / 128, 128, 0, s>>>(fd.sx, fd.N, fd.nvx, maxes + 2);
   k_shift_spread<<<(fd.nvy + 127) / 128, 128, 0, s>>>(fd.sy, fd.N, fd.nvy, maxes + 2);
   cudaMemcpyAsync(fp->h_maxes, maxes, sizeof(int) * 3, cudaMemcpyDeviceToHost, s);
@@ -760,7 +902,10 @@ int fast_prepare(const FieldDev& fd, FastPlan* fp, cudaStream_t s, bool* fits) {
   if (cudaGetLastError() != cudaSuccess) return 1;
   // N >= 8: the producer runs at most S*F = 24 frames ahead of the consumers,
   // so at most 4 items are live and the 8 per-item slots never collide.
-  const int ocol_max = fd.storage == ST_F32 ? Store<float>::kOColMax : Store<__half>::kOColMax;
+  // bilinear reads one more column: lane 31 + ocol + 1 must stay in the box
+  const int ocol_max = fd.storage == ST_F32
+                           ? Store<float>::kBoxW - kTX - (fp->bl ? 1 : 0)
+                           : Store<__half>::kOColMax;
   *fits = fp->h_maxes[0] <= ocol_max && fp->h_maxes[1] < kPatterns && fd.N <= kParamBytes &&
           fd.N >= 8;
   return 1;
@@ -772,9 +917,9 @@ int launch_stack_fast(const FieldDev& fd, const FastPlan* cfp, int k0, int nk,
   FastPlan* fp = const_cast<FastPlan*>(cfp);
   if (k0 != 0 || nk != fd.nvx * fd.nvy || dump_k) return -1;  // whole grid only
   int nvar = 0;
-  const Variant* vars = variants_for(fd.storage, &nvar);
+  const Variant* vars = variants_for(fd.storage, fp->bl, &nvar);
   const Variant& var = vars[fp->variant < nvar ? fp->variant : 0];
-  const int ky = var.ky, boxh = ky + 3;
+  const int ky = var.ky, boxh = ky + 3 + (fp->bl ? 1 : 0);
   const int esz = fd.storage == ST_F32 ? 4 : 2;
   const int boxw = fd.storage == ST_F32 ? Store<float>::kBoxW : Store<__half>::kBoxW;
   const CUtensorMapDataType dtype = fd.storage == ST_F32    ? Store<float>::kTma
@@ -820,6 +965,10 @@ int launch_stack_fast(const FieldDev& fd, const FastPlan* cfp, int k0, int nk,
   a.ymax = fp->ranges + 2 * fp->nA + fp->nB;
   a.sx = fd.sx;
   a.sy = fd.sy;
+  a.fx = fd.fx;
+  a.fy = fd.fy;
+  a.fxt = reinterpret_cast<const float4*>(fp->fxt);
+  a.fyt = reinterpret_cast<const float4*>(fp->fyt);
   a.thr = fd.thr;
   a.cov_len = fp->cov_len;
   a.covx = fp->cov;
@@ -835,11 +984,11 @@ int launch_stack_fast(const FieldDev& fd, const FastPlan* cfp, int k0, int nk,
   a.dump_C = dump_C;
   void (*fn)(CUtensorMap, FastArgs) = dump_S ? var.dump_fn : var.fn;
   size_t smem = (size_t)var.stages * stage_bytes + 128;
-  static bool attr_set[3][2 * kNumVariants] = {};
+  static bool attr_set[2][3][2 * kNumVariants] = {};
   const int attr_i = 2 * (fp->variant < nvar ? fp->variant : 0) + (dump_S ? 1 : 0);
-  if (!attr_set[fd.storage][attr_i]) {
+  if (!attr_set[fp->bl][fd.storage][attr_i]) {
     cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set[fd.storage][attr_i] = true;
+    attr_set[fp->bl][fd.storage][attr_i] = true;
   }
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);

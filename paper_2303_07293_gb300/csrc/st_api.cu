@@ -174,10 +174,10 @@ st_status check_times(const double* t, int N, const st_field& f, int idx) {
 size_t store_bytes(int storage) { return storage == ST_F32 ? 4 : 2; }
 
 // Autotuning cache: a flat JSON object {"<field key>": variant, ...}.
-std::string tune_key(const st_field& f, int storage, int sms) {
+std::string tune_key(const st_field& f, int storage, int mode, int sms) {
   char b[160];
-  snprintf(b, sizeof b, "W%d_H%d_N%d_nvx%d_nvy%d_st%d_sm%d", f.width, f.height, f.n_frames, f.nvx,
-           f.nvy, storage, sms);
+  snprintf(b, sizeof b, "W%d_H%d_N%d_nvx%d_nvy%d_st%d_m%d_sm%d", f.width, f.height, f.n_frames,
+           f.nvx, f.nvy, storage, mode, sms);
   return b;
 }
 
@@ -284,9 +284,9 @@ st_status device_search(st_plan_t* p, const float* const* d_frames, const double
       L += fast_prepare(fds[fi], fp.fast, p->s, &fits);
       CK(cudaGetLastError());
       if (fits && p->o.tile == -1 && !fp.tuned) {
-        const std::string key = tune_key(fp.f, fds[fi].storage, p->sms);
+        const std::string key = tune_key(fp.f, fds[fi].storage, p->o.mode, p->sms);
         int v = tune_lookup(p->tune_cache, key);
-        if (v >= 0 && v < fast_num_variants_for(fds[fi].storage)) {
+        if (v >= 0 && v < fast_num_variants_for(fp.fast, fds[fi].storage)) {
           fast_set_variant(fp.fast, v);
         } else {
           L += fast_autotune(fds[fi], fp.fast, 8ll * p->sms, p->d_pend, p->pend_cap, p->d_ctr,
@@ -423,7 +423,7 @@ st_status st_plan(const st_field* fields, int32_t n_fields, const st_opts* opts,
             "cudaMalloc(cube)");
     if (st == ST_OK && opts->tile != 1) {
       FieldDev probe = field_dev(fp, nullptr, i, opts->storage);
-      if (fast_eligible(probe, opts->mode) && !fast_plan_build(probe, nullptr, nullptr, &fp.fast, p->s))
+      if (fast_eligible(probe, opts->mode) && !fast_plan_build(probe, opts->mode, &fp.fast))
         st = fail(ST_ERR_OOM, "field %d: fast-kernel tables could not be allocated", i);
       if (fp.fast && opts->tile >= 2) fast_set_variant(fp.fast, opts->tile - 2);
     }

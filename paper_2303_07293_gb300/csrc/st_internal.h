@@ -72,25 +72,24 @@ int launch_stack_generic(const FieldDev& fd, int mode, int k0, int nk, const int
                          float* dump_S, int32_t* dump_C, Pending* pend, int64_t pend_cap,
                          Counters* ctr, cudaStream_t s);
 
-// Fast nearest-pixel stack kernel (register-window reuse); returns -1 when the
-// field's geometry does not fit the kernel (caller falls back).
+// Register-window stack kernel (nearest or bilinear sampling); returns -1 when
+// the field's geometry does not fit the kernel (caller falls back).
 struct FastPlan;
 int fast_plan_size_bytes();
 int fast_num_variants();
-int fast_num_variants_for(int storage);
+int fast_num_variants_for(const FastPlan* fp, int storage);
 int fast_get_variant(const FastPlan* fp);
 int fast_autotune(const FieldDev& fd, FastPlan* fp, int64_t items, Pending* pend,
                   int64_t pend_cap, Counters* ctr, cudaStream_t s);
 const char* fast_variant_name(int v);
 void fast_set_variant(FastPlan* fp, int v);
-// Whether the field can use the fast kernel at all (nearest, FP32 storage,
-// width a multiple of 4).
+// Whether the field can use the fast kernel at all (width a multiple of
+// 16 bytes for the tensor map).
 bool fast_eligible(const FieldDev& fd, int mode);
 // Builds the per-frame tile tables for the current shift tables; *fits tells
 // whether the motion spans fit the kernel.  Synchronises the stream.
 int fast_prepare(const FieldDev& fd, FastPlan* fp, cudaStream_t s, bool* fits);
-bool fast_plan_build(const FieldDev& fd, const int32_t* h_sx, const int32_t* h_sy,
-                     FastPlan** out, cudaStream_t s);
+bool fast_plan_build(const FieldDev& fd, int mode, FastPlan** out);
 void fast_plan_free(FastPlan* fp);
 int launch_stack_fast(const FieldDev& fd, const FastPlan* fp, int k0, int nk,
                       const int32_t* dump_k, float* dump_S, int32_t* dump_C, Pending* pend,
