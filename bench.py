@@ -32,6 +32,8 @@ WORKLOADS = {
     "tiny": dict(name="tiny", desc="128x128x16, 21x21 velocity grid"),
     "batched": dict(name="batched", desc="24 fields: N in [40,400], sizes {512,1024,2048}^2, "
                     "baselines 1-8 h, grid step 1 px/baseline, +-60 px/h, one plan"),
+    "refine": dict(name="refine", desc="4096 candidates of a 2048x2048x300 field's 801x801 grid "
+                   "search, 64x64 cutouts, 20 Adam steps"),
 }
 METRIC = "G pixel*frame*velocity adds/s (2048x2048x256, 801x801 grid)"
 
@@ -118,9 +120,10 @@ def measured_peaks():
         return {}
 
 
-def oracle_baseline(d, seconds, rank0=True):
-    """Oracle (FP32-sequential, as it stands) on a slab of velocity planes of
-    the same field; returns (adds/s, cores, sample description, elapsed)."""
+def oracle_baseline(d, seconds, mode="nearest"):
+    """Oracle (as it stands: FP32-sequential nearest, FP64 bilinear) on a slab
+    of velocity planes of the same field; returns (adds/s, cores, sample
+    description, elapsed)."""
     import oracle
     oracle.lib()  # build/load outside the timed region
     f = d["field"]
@@ -130,27 +133,190 @@ def oracle_baseline(d, seconds, rank0=True):
     nk = f["nvx"] * f["nvy"]
     k0 = nk // 2 - cores // 2
     t0 = time.perf_counter()
-    oracle.search(fr, d["times"], f, prec="fp32", k_begin=k0, k_end=k0 + cores)
+    prec = "fp64" if mode == "bilinear" else "fp32"
+    oracle.search(fr, d["times"], f, mode=mode, prec=prec, k_begin=k0, k_end=k0 + cores)
     dt = time.perf_counter() - t0
     per_round = dt
     rounds = max(1, int(seconds / max(per_round, 1e-3)) - 1)
     k1 = min(nk, k0 + cores + rounds * cores)
     t0 = time.perf_counter()
-    oracle.search(fr, d["times"], f, prec="fp32", k_begin=k0 + cores, k_end=k1)
+    oracle.search(fr, d["times"], f, mode=mode, prec=prec, k_begin=k0 + cores, k_end=k1)
     el = time.perf_counter() - t0
     n_planes = k1 - (k0 + cores)
     adds = float(W * H * N) * n_planes
+    kind = "FP64 bilinear" if mode == "bilinear" else "FP32-sequential nearest"
     return adds / el, cores, (f"{n_planes} velocity planes (k {k0 + cores}..{k1 - 1}) of the "
-                              f"full {W}x{H}x{N} field, FP32-sequential oracle"), el
+                              f"full {W}x{H}x{N} field, {kind} oracle"), el
 
 
 def field_for(args, rank):
     import synth
     w = WORKLOADS[args.workload]["name"]
-    seed = synth.BASE_SEED + {"tiny": 1, "mid": 2, "speculoos": 3, "batched": 4}[w] + 100000 * rank
+    seed = synth.BASE_SEED + {"tiny": 1, "mid": 2, "speculoos": 3, "batched": 4,
+                              "refine": 5}[w] + 100000 * rank
     if w == "batched":
         return [synth.make_field(w, seed=seed, index=j) for j in range(24)]
     return synth.make_field(w, seed=seed)
+
+
+REFINE_N, REFINE_STEPS, REFINE_CUT = 4096, 20, 64
+
+
+def refine_units(N, steps=REFINE_STEPS):
+    """Bilinear cutout samples of one refinement call: candidates x cutout
+    pixels x frames x (steps + 1) objective evaluations."""
+    return float(REFINE_N) * REFINE_CUT * REFINE_CUT * N * (steps + 1)
+
+
+def refine_reference(args, d, config):
+    """The FP64 refinement oracle on a bounded sample of the candidates (one
+    objective-and-gradient evaluation each, at the injected movers' grid
+    points), scaled to samples/s."""
+    import oracle
+    oracle.lib()
+    fr = np.nan_to_num(d["frames"], nan=0.0)
+    N = fr.shape[0]
+    tr = d["truth"]
+    cores = oracle.num_threads()
+    th = np.array([[m[2], m[3], m[0], m[1], m[4]] for m in tr], np.float64)
+    ce = np.rint(th[:, 2:4]).astype(np.int32)
+    t0 = time.perf_counter()
+    oracle.refine_eval(fr, d["times"], d["field"]["t_ref"], th[:cores], ce[:cores])
+    one = (time.perf_counter() - t0) / min(cores, len(th))
+    n = int(max(1, min(len(th), max(1.0, args.cpu_seconds / 3) / max(one, 1e-6))))
+    vals = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.refine_eval(fr, d["times"], d["field"]["t_ref"], th[:n], ce[:n])
+        el = time.perf_counter() - t0
+        if s >= args.warmup:
+            vals.append(n * REFINE_CUT * REFINE_CUT * N / el / 1e9)
+    v = float(np.median(vals))
+    sample = (f"{n} candidates x one FP64 objective+gradient evaluation of a {REFINE_CUT}^2 "
+              f"cutout over {N} frames")
+    print(json.dumps({
+        "impl": "reference", "metric": REFINE_METRIC, "value": v, "unit": "G samples/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config,
+        "cpu_baseline": {"value": v, "unit": "G samples/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "G samples/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}))
+
+
+REFINE_METRIC = ("G bilinear cutout samples/s (4096 candidates x 64^2 px x 300 frames x 21 "
+                 "evaluations)")
+
+
+def bench_refine(args, d, config, dev, world, rank, local):
+    """Row a9: st_refine on the 4096 highest-SNR candidates of the field's
+    grid search (the search itself is set-up, not timed)."""
+    import torch
+    import paper_2303_07293_gb300 as st
+    f = d["field"]
+    N, H, W = d["frames"].shape
+    stream = torch.cuda.current_stream(dev)
+    frames = torch.from_numpy(d["frames"]).to(dev)
+    plan = st.Plan(f, storage=args.storage, normalize=bool(args.normalize),
+                   cr_clip=args.cr_clip if args.normalize else 0.0, tile=args.tile,
+                   pending_capacity=1 << 24, stream=stream)
+    cap = 1 << 22
+    out = torch.empty((cap, 7), dtype=torch.int32, device=dev)
+    _, n, status = plan.search(frames, d["times"], capacity=cap, out=out)
+    if status != st.ST_OK:
+        raise RuntimeError(f"search status {status}")
+    recs = out[:n].cpu().numpy().view(st.CAND_DTYPE).reshape(-1)
+    order = np.argsort(-recs["snr"], kind="stable")[:REFINE_N]
+    top = recs[order]
+    if len(top) < REFINE_N:  # a quiet field: repeat the list to the batch size
+        top = np.resize(top, REFINE_N)
+    cands = torch.from_numpy(np.ascontiguousarray(top).view(np.int32).reshape(-1, 7)).to(dev)
+
+    def step():
+        return plan.refine(cands, steps=REFINE_STEPS)
+
+    for _ in range(args.warmup):
+        rec = step()
+    clocks = Clocks(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        rec = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_step = ev0.elapsed_time(ev1) / 1e3 / args.steps
+    if world > 1:
+        tt = torch.tensor([t_step], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(tt.item())
+    units = refine_units(N)
+    value = units * world / t_step / 1e9
+    # end to end: candidates from pinned host memory, refined records back
+    hc = torch.from_numpy(np.ascontiguousarray(top).view(np.int32).reshape(-1, 7)).pin_memory()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        dc = hc.to(dev, non_blocking=True)
+        rec = plan.refine(dc, steps=REFINE_STEPS)
+    te = (time.perf_counter() - t0) / args.steps
+    if rank != 0:
+        return
+    # algorithmic work per sample of the plain definition: the bilinear
+    # sample (4 FMA) and its two slopes dB/dX, dB/dY (2 subtractions, a
+    # product and an FMA each) weighted by g into their sums (1 FMA each)
+    ops_per_sample = 14.0
+    props = torch.cuda.get_device_properties(dev)
+    peaks = measured_peaks()
+    max_mhz = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    peak_t = props.multi_processor_count * 128 * max_mhz * 1e6 / 1e12
+    achieved = ops_per_sample * units / t_step / 1e12
+    # algorithmic bytes: each evaluation reads, per candidate and frame, the
+    # (64+1)^2 taps of its cutout footprint once (L2 serves overlapping
+    # footprints, so this can exceed the copy bandwidth)
+    esz = 4 if args.storage == "f32" else 2
+    bytes_call = float(REFINE_N) * (REFINE_CUT + 1) ** 2 * esz * N * (REFINE_STEPS + 1)
+    hbm = peaks.get("hbm_gbs", 6780.0)
+    gbs = bytes_call / t_step / 1e9
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_t, "unit": "T FP32 ops/s",
+            "frac": achieved / peak_t, "traffic": None, "work_per_unit": ops_per_sample,
+            "kernel": "refine (bilinear cutout forward + adjoint, Adam)",
+            "launches_per_step": 1, "avg_launch_ms": t_step * 1e3,
+            "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz",
+            "footprint_gbs": gbs, "footprint_frac_of_hbm": gbs / hbm,
+            "bytes_per_call": bytes_call}
+    cfg = dict(config, candidates=REFINE_N, cutout=REFINE_CUT, adam_steps=REFINE_STEPS,
+               frames=N, storage=args.storage)
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        import io
+        import contextlib
+        buf = io.StringIO()
+        a2 = argparse.Namespace(**vars(args))
+        a2.warmup, a2.steps = 0, 1
+        with contextlib.redirect_stdout(buf):
+            refine_reference(a2, d, config)
+        r = json.loads(buf.getvalue())
+        cpu = r["cpu_baseline"]
+    snr_gain = float(np.median(rec["snr"] / np.maximum(top["snr"], 1e-6)))
+    line = {
+        "metric": REFINE_METRIC, "value": value, "unit": "G samples/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": cfg, "roofline": roof, "cpu_baseline": cpu,
+        "clocks": clk, "median_snr_gain": snr_gain,
+        "e2e": {"value": units * world / te / 1e9, "unit": "G samples/s",
+                "h2d_bytes_per_step": int(hc.numel() * 4),
+                "d2h_bytes_per_step": int(REFINE_N * 32), "s_per_step": te},
+        "gpu_launches": int(plan.last_launch_count()) * args.steps,
+        "device": torch.cuda.get_device_properties(dev).name}
+    print(json.dumps(line))
+    plan.close()
 
 
 def main():
@@ -177,21 +343,24 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        rate, cores, sample, el = oracle_baseline(d, max(1.0, args.cpu_seconds / 3))
+        if args.workload == "refine":
+            return refine_reference(args, d, config)
+        unit = "G samples/s" if args.mode == "bilinear" else "G adds/s"
+        rate, cores, sample, el = oracle_baseline(d, max(1.0, args.cpu_seconds / 3), args.mode)
         times = []
         for s in range(args.warmup + args.steps):
-            r, cores, sample, el = oracle_baseline(d, max(1.0, args.cpu_seconds / 3))
+            r, cores, sample, el = oracle_baseline(d, max(1.0, args.cpu_seconds / 3), args.mode)
             if s >= args.warmup:
                 times.append(r)
         v = float(np.median(times)) / 1e9
         print(json.dumps({
-            "impl": "reference", "metric": METRIC, "value": v, "unit": "G adds/s",
+            "impl": "reference", "metric": METRIC, "value": v, "unit": unit,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": config,
-            "cpu_baseline": {"value": v, "unit": "G adds/s", "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": unit, "cores": cores, "kind": "oracle",
                              "sample": sample},
-            "e2e": {"value": v, "unit": "G adds/s", "h2d_bytes_per_step": 0,
+            "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}))
         return
 
@@ -202,6 +371,8 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     import paper_2303_07293_gb300 as st
+    if args.workload == "refine":
+        return bench_refine(args, d, config, dev, world, rank, local)
 
     frames = [torch.from_numpy(x["frames"]).to(dev) for x in ds]
     times = [x["times"] for x in ds]
@@ -288,26 +459,33 @@ def main():
     sms = props.multi_processor_count
     peaks = measured_peaks()
     max_mhz = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    peak_t = sms * 128 * max_mhz * 1e6 / 1e12  # FP32 adds per second, T
+    peak_t = sms * 128 * max_mhz * 1e6 / 1e12  # FP32 adds (or FMAs) per second, T
     stack_avg_ms = stack_ms / max(stack_launch, 1)
-    achieved = adds / (stack_ms / 1e3 / args.steps) / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak_t, "unit": "T adds/s",
-            "frac": achieved / peak_t, "traffic": None,
+    # algorithmic work per pixel*frame*velocity: 1 add (nearest), 4 FMA (bilinear)
+    per_unit = 4.0 if args.mode == "bilinear" else 1.0
+    achieved = per_unit * adds / (stack_ms / 1e3 / args.steps) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_t,
+            "unit": "T FMA/s" if args.mode == "bilinear" else "T adds/s",
+            "frac": achieved / peak_t, "traffic": None, "work_per_unit": per_unit,
             "kernel": "stack (shift-and-stack + threshold)", "launches_per_step":
                 stack_launch / args.steps, "avg_launch_ms": stack_avg_ms,
             "peak_basis": f"{sms} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz (max SM clock)"}
     if clk and clk.get("sm_mhz"):
         roof["frac_at_observed_clock"] = achieved / (sms * 128 * clk["sm_mhz"] * 1e6 / 1e12)
+    unit = "G samples/s" if args.mode == "bilinear" else "G adds/s"
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        rate, cores, sample, el = oracle_baseline(d, args.cpu_seconds)
-        cpu = {"value": rate / 1e9, "unit": "G adds/s", "cores": cores, "kind": "oracle",
+        rate, cores, sample, el = oracle_baseline(d, args.cpu_seconds, args.mode)
+        cpu = {"value": rate / 1e9, "unit": unit, "cores": cores, "kind": "oracle",
                "sample": sample, "seconds": el}
+    if e2e:
+        e2e["unit"] = unit
     line = {
-        "metric": METRIC, "value": value, "unit": "G adds/s", "n_gpus": args.gpus,
+        "metric": METRIC, "value": value, "unit": unit, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "config": config, "fields_per_hr": 3600.0 / t_step * world,
+        "data": "synthetic", "config": config,
+        "fields_per_hr": 3600.0 / t_step * world * len(ds),
         "candidates": int(n_found), "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
         "e2e": e2e, "gpu_launches": int(launches), "device": props.name}
     print(json.dumps(line))

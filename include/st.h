@@ -173,7 +173,12 @@ st_status st_stack_search_host(st_plan_t* plan, const float* const* h_frames,
  * (optimizer 0 = Adam, lr_pos px for x0, y0 and lr_vel for vx, vy) maximise J.
  * d_in: device candidates; d_out: device results [n]; d_grad_out: optional
  * device [n][5] gradient dJ/dtheta at the final parameters (order vx, vy, x0,
- * y0, F).  Requires a prior st_stack_search on the plan (frames resident). */
+ * y0, F).  Requires a prior st_stack_search on the plan (frames resident).
+ * The frames are staged per candidate by TMA tile copies: returns
+ * ST_ERR_UNSUPPORTED when a field's row (width x element size) is not a
+ * multiple of 16 bytes or it has more than 8192 frames, and ST_ERR_TIMEOUT
+ * when a copy does not land within 2 s (the kernel exits cleanly).
+ * Synchronises the plan's stream. */
 st_status st_refine(st_plan_t* plan, const st_candidate* d_in, int64_t n,
                     int32_t steps, int32_t optimizer, float fwhm, float lr_pos,
                     float lr_vel, st_refined* d_out, float* d_grad_out);
@@ -182,7 +187,7 @@ st_status st_refine(st_plan_t* plan, const st_candidate* d_in, int64_t n,
  * building block of the autograd binding.  theta: device [n][5] (vx, vy, x0,
  * y0, F); centre: device [n][2] int32 cutout centres; fields: device [n]
  * int32.  Writes J [n], SNR [n] and, if d_grad is not NULL, dJ/dtheta [n][5].
- * Frames are those of the plan's last search. */
+ * Frames are those of the plan's last search; errors as st_refine. */
 st_status st_refine_eval(st_plan_t* plan, const float* d_theta,
                          const int32_t* d_centre, const int32_t* d_field,
                          int64_t n, float fwhm, float* d_J, float* d_snr,

@@ -11,14 +11,25 @@
 // the bilinear cell).  The samples and their derivatives are recomputed on
 // every evaluation, never stored.
 //
-// One CTA per candidate; thread t owns cutout row t/4 and 16 consecutive
-// columns (t%4)*16.., so its pixels share one bilinear fraction per frame and
-// their taps are contiguous.  Reductions use a fixed-order block tree.
+// One CTA per candidate.  Every pixel of the cutout shares a frame's shift,
+// so a frame contributes one footprint of 65 x 65 taps; a TMA ring of S
+// frames stages those footprints in shared memory ahead of use (zero fill
+// outside the image takes the place of bounds tests; the box x origin is
+// rounded down to 16 bytes and the remainder is an index offset).  Thread t
+// owns cutout column t%64 and its 16 rows (t/64)*16.., so a warp reads 32
+// consecutive words of a box row; it walks its rows with the horizontal
+// interpolation h = a0 + fx (a1 - a0) of the row below carried over, so each
+// tap row is read and interpolated once.  Reductions use a fixed-order block
+// tree.  Every wait is bounded in time.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <vector>
+
 #include "st_internal.h"
 #include "st_sample.cuh"
+#include "st_tma.cuh"
 
 namespace st {
 
@@ -26,11 +37,22 @@ namespace {
 
 constexpr int kCut = 64;        // cutout side
 constexpr int kThreads = 256;
-constexpr int kPix = kCut * kCut / kThreads;  // 16 pixels per thread
+constexpr int kPix = kCut * kCut / kThreads;  // 16 rows of one column per thread
 constexpr int kSums = 8;
+constexpr int kBoxW = 72;       // footprint columns: 65 taps + up to 7 of alignment
+constexpr int kBoxH = kCut + 1; // footprint rows
+constexpr uint64_t kWaitNs = 2000000000ull;  // wait limit: 2 s of wall-clock time
+
+template <typename T>
+constexpr int stages_for() { return sizeof(T) == 4 ? 4 : 6; }
+template <typename T>
+constexpr int box_bytes() { return ((kBoxW * kBoxH * (int)sizeof(T)) + 127) & ~127; }
+template <typename T>
+constexpr int align_elems() { return 16 / (int)sizeof(T); }
 
 struct RefineArgs {
   const FieldDev* fds;          // device field descriptors
+  const CUtensorMap* maps;      // per field: tiled map of the cube, box kBoxW x kBoxH x 1
   const double* const* times;   // per field: device FP64 timestamps
   const double* t_ref;          // per field
   const float* theta_in;        // [n][5] (eval mode)
@@ -46,11 +68,18 @@ struct RefineArgs {
   float* snr;
   float* grad;                  // [n][5] or null
   st_refined* out;              // optimise mode
+  int* err;                     // timeout flag
 };
 
 template <typename T>
-__device__ __forceinline__ float pxv(const T* fr, int W, int H, int u, int v) {
-  return (u >= 0 && v >= 0 && u < W && v < H) ? load_px<T>(fr + (int64_t)v * W + u) : 0.0f;
+__device__ __forceinline__ float ld_s(const T* p);
+template <>
+__device__ __forceinline__ float ld_s<float>(const float* p) { return *p; }
+template <>
+__device__ __forceinline__ float ld_s<__half>(const __half* p) { return __half2float(*p); }
+template <>
+__device__ __forceinline__ float ld_s<__nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat162float(*p);
 }
 
 // Fixed-order block reduction of kSums values; result valid in thread 0.
@@ -73,69 +102,6 @@ __device__ void block_sum(float (&v)[kSums], float* sh) {
   __syncthreads();
 }
 
-// Sums for one candidate at theta: <g,S>, <g,g>, <gx,S>, <gy,S>, <g,gx>,
-// <g,gy>, sum g dS/dvx, sum g dS/dvy (valid in thread 0).
-template <typename T>
-__device__ void evaluate(const FieldDev& fd, const double* t, double t_ref, int cx, int cy,
-                         float vx, float vy, float x0, float y0, float inv2s2, float inv_s2,
-                         float (&sums)[kSums], float* sh) {
-  const int row = threadIdx.x / 4;
-  const int col0 = (threadIdx.x % 4) * kPix;
-  const float py = (float)(cy - kCut / 2 + row);
-  const float px0 = (float)(cx - kCut / 2 + col0);
-  float S[kPix];
-  float g[kPix];
-  const float dy0 = py - y0;
-#pragma unroll
-  for (int k = 0; k < kPix; ++k) {
-    S[k] = 0.0f;
-    const float dx = px0 + (float)k - x0;
-    g[k] = expf(-(dx * dx + dy0 * dy0) * inv2s2);
-  }
-  float dvx = 0.0f, dvy = 0.0f;
-  const T* cube = (const T*)fd.cube;
-  const int64_t P = (int64_t)fd.W * fd.H;
-  for (int i = 0; i < fd.N; ++i) {
-    const float dt = (float)(t[i] - t_ref);
-    const float X = px0 + vx * dt, Y = py + vy * dt;
-    const float fxl = floorf(X), fyl = floorf(Y);
-    const float fx = X - fxl, fy = Y - fyl;
-    const int u = (int)fxl, v = (int)fyl;
-    const T* fr = cube + (int64_t)i * P;
-    float a0 = pxv<T>(fr, fd.W, fd.H, u, v), b0 = pxv<T>(fr, fd.W, fd.H, u, v + 1);
-    float gdx = 0.0f, gdy = 0.0f;
-#pragma unroll
-    for (int k = 0; k < kPix; ++k) {
-      const float a1 = pxv<T>(fr, fd.W, fd.H, u + k + 1, v);
-      const float b1 = pxv<T>(fr, fd.W, fd.H, u + k + 1, v + 1);
-      const float top = a0 + fx * (a1 - a0), bot = b0 + fx * (b1 - b0);
-      S[k] += top + fy * (bot - top);
-      gdx += g[k] * ((1.0f - fy) * (a1 - a0) + fy * (b1 - b0));
-      gdy += g[k] * (bot - top);
-      a0 = a1;
-      b0 = b1;
-    }
-    dvx += dt * gdx;
-    dvy += dt * gdy;
-  }
-#pragma unroll
-  for (int k = 0; k < kSums; ++k) sums[k] = 0.0f;
-#pragma unroll
-  for (int k = 0; k < kPix; ++k) {
-    const float gx = g[k] * (px0 + (float)k - x0) * inv_s2;
-    const float gy = g[k] * dy0 * inv_s2;
-    sums[0] += g[k] * S[k];
-    sums[1] += g[k] * g[k];
-    sums[2] += gx * S[k];
-    sums[3] += gy * S[k];
-    sums[4] += g[k] * gx;
-    sums[5] += g[k] * gy;
-  }
-  sums[6] = dvx;
-  sums[7] = dvy;
-  block_sum(sums, sh);
-}
-
 __device__ void objective(const float (&s)[kSums], int N, float F, float* J, float* snr,
                           float (&gr)[5]) {
   const float nf = (float)N;
@@ -148,10 +114,28 @@ __device__ void objective(const float (&s)[kSums], int N, float F, float* J, flo
   gr[4] = s[0] - F * nf * s[1];
 }
 
+// A frame's shift for velocity (vx, vy): integer parts and fractions.
+struct Shift {
+  int ux, uy;
+  float fx, fy;
+};
+__device__ __forceinline__ Shift frame_shift(float vx, float vy, float dt) {
+  const float sxv = vx * dt, syv = vy * dt;
+  const float fxl = floorf(sxv), fyl = floorf(syv);
+  return Shift{(int)fxl, (int)fyl, sxv - fxl, syv - fyl};
+}
+
 template <typename T, bool OPT>
-__global__ void __launch_bounds__(kThreads) k_refine(RefineArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) k_refine(RefineArgs a) {
+  constexpr int S = stages_for<T>();
+  constexpr int kBox = box_bytes<T>();
+  constexpr int kAl = align_elems<T>();
+  extern __shared__ __align__(128) unsigned char dsm_raw[];
+  __shared__ __align__(8) uint64_t full[S];
   __shared__ float sh[(kThreads / 32) * kSums];
   __shared__ float th[5];
+  __shared__ int s_ok;
+  unsigned char* ring = dsm_raw + ((128u - (smem_u32(dsm_raw) & 127u)) & 127u);
   const int64_t c = blockIdx.x;
   if (c >= a.n) return;
   int fi, cx, cy;
@@ -166,9 +150,20 @@ __global__ void __launch_bounds__(kThreads) k_refine(RefineArgs a) {
     cy = a.centre_in[2 * c + 1];
   }
   const FieldDev& fd = a.fds[fi];
-  const double* t = a.times[fi];
-  const double t_ref = a.t_ref[fi];
-  if (threadIdx.x == 0) {
+  const int N = fd.N;
+  float* sdt = reinterpret_cast<float*>(ring + (size_t)S * kBox);  // [N] FP32 time offsets
+  const CUtensorMap* map = a.maps + fi;
+  const int tid = threadIdx.x;
+  {
+    const double* t = a.times[fi];
+    const double t_ref = a.t_ref[fi];
+    for (int j = tid; j < N; j += kThreads) sdt[j] = (float)(t[j] - t_ref);
+  }
+  if (tid == 0) {
+    tma_prefetch_desc(map);
+    for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
+    mbar_init_fence();
+    s_ok = 1;
     if (OPT) {
       const st_candidate cd = a.cand[c];
       const double* gr = a.grid + 4 * fi;
@@ -182,16 +177,103 @@ __global__ void __launch_bounds__(kThreads) k_refine(RefineArgs a) {
     }
   }
   __syncthreads();
+
+  // thread 0 stages frame i (sequence number q) into ring slot q % S
+  uint32_t q_issued = 0;  // (thread 0) sequence number after the last staged frame
+  auto issue = [&](int i, uint32_t q, float vx, float vy) {
+    q_issued = q + 1;
+    const Shift f = frame_shift(vx, vy, sdt[i]);
+    const int cu0 = cx - kCut / 2 + f.ux, cv0 = cy - kCut / 2 + f.uy;
+    const int bx = cu0 & ~(kAl - 1);  // 16-byte aligned box origin (floor, also below 0)
+    const int slot = (int)(q % S);
+    mbar_arrive_expect_tx(&full[slot], (uint32_t)(kBoxW * kBoxH * sizeof(T)));
+    tma_load_3d(ring + (size_t)slot * kBox, map, bx, cv0, i, &full[slot]);
+  };
+
+  const int col = tid % kCut;
+  const int row0 = (tid / kCut) * kPix;
+  const float fcol = (float)(cx - kCut / 2 + col);
+  const float frow0 = (float)(cy - kCut / 2 + row0);
   float sums[kSums];
   float m[4] = {0, 0, 0, 0}, v2[4] = {0, 0, 0, 0};
   const int steps = OPT ? a.steps : 0;
-  for (int step = 0; step <= steps; ++step) {
-    evaluate<T>(fd, t, t_ref, cx, cy, th[0], th[1], th[2], th[3], a.inv2s2, a.inv_s2, sums, sh);
-    if (threadIdx.x == 0) {
+  uint32_t q0 = 0;  // frames staged before this evaluation
+  bool ok = true;
+  for (int step = 0; step <= steps && ok; ++step) {
+    const float vx = th[0], vy = th[1], x0 = th[2], y0 = th[3];
+    if (tid == 0)
+      for (int i = 0; i < S && i < N; ++i) issue(i, q0 + i, vx, vy);
+    float S_[kPix], g[kPix];
+    const float dx = fcol - x0;
+#pragma unroll
+    for (int k = 0; k < kPix; ++k) {
+      S_[k] = 0.0f;
+      const float dy = frow0 + (float)k - y0;
+      g[k] = expf(-(dx * dx + dy * dy) * a.inv2s2);
+    }
+    float dvx = 0.0f, dvy = 0.0f;
+    for (int i = 0; i < N; ++i) {
+      const uint32_t q = q0 + i;
+      const int slot = (int)(q % S);
+      if (!mbar_wait(&full[slot], (q / S) & 1u, kWaitNs)) {
+        atomicOr(a.err, 1);
+        s_ok = 0;
+      }
+      const float dt = sdt[i];
+      const Shift f = frame_shift(vx, vy, dt);
+      const int cu0 = cx - kCut / 2 + f.ux;
+      const T* box = reinterpret_cast<const T*>(ring + (size_t)slot * kBox) +
+                     (size_t)row0 * kBoxW + (cu0 - (cu0 & ~(kAl - 1))) + col;
+      float a0 = ld_s<T>(box), a1 = ld_s<T>(box + 1);
+      float dp = a1 - a0;        // a1 - a0 of the row above
+      float hp = a0 + f.fx * dp; // its horizontal interpolation (top)
+      float gdx = 0.0f, gdy = 0.0f;
+#pragma unroll
+      for (int k = 0; k < kPix; ++k) {
+        const T* r = box + (k + 1) * kBoxW;
+        const float b0 = ld_s<T>(r), b1 = ld_s<T>(r + 1);
+        const float d = b1 - b0;
+        const float h = b0 + f.fx * d;   // bottom
+        const float dh = h - hp;         // bot - top
+        S_[k] += hp + f.fy * dh;
+        gdx += g[k] * (dp + f.fy * (d - dp));  // (1-fy)(a1-a0) + fy(b1-b0)
+        gdy += g[k] * dh;
+        hp = h;
+        dp = d;
+      }
+      dvx += dt * gdx;
+      dvy += dt * gdy;
+      __syncthreads();  // every thread is done with the slot
+      if (!s_ok) {
+        ok = false;
+        break;
+      }
+      if (tid == 0 && i + S < N) issue(i + S, q + S, vx, vy);
+    }
+    if (!ok) break;
+    q0 += (uint32_t)N;
+#pragma unroll
+    for (int k = 0; k < kSums; ++k) sums[k] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kPix; ++k) {
+      const float dy = frow0 + (float)k - y0;
+      const float gx = g[k] * dx * a.inv_s2;
+      const float gy = g[k] * dy * a.inv_s2;
+      sums[0] += g[k] * S_[k];
+      sums[1] += g[k] * g[k];
+      sums[2] += gx * S_[k];
+      sums[3] += gy * S_[k];
+      sums[4] += g[k] * gx;
+      sums[5] += g[k] * gy;
+    }
+    sums[6] = dvx;
+    sums[7] = dvy;
+    block_sum(sums, sh);
+    if (tid == 0) {
       // F at its optimum <g,S>/(N <g,g>) when optimising (profile likelihood)
-      if (OPT) th[4] = sums[1] > 0.0f ? sums[0] / ((float)fd.N * sums[1]) : 0.0f;
+      if (OPT) th[4] = sums[1] > 0.0f ? sums[0] / ((float)N * sums[1]) : 0.0f;
       float J, snr, gr[5];
-      objective(sums, fd.N, th[4], &J, &snr, gr);
+      objective(sums, N, th[4], &J, &snr, gr);
       if (step == steps) {
         if (a.J) a.J[c] = J;
         if (a.snr) a.snr[c] = snr;
@@ -224,18 +306,49 @@ __global__ void __launch_bounds__(kThreads) k_refine(RefineArgs a) {
     }
     __syncthreads();
   }
+  if (!ok && tid == 0) {
+    // a wait gave up: let the copies already issued land (bounded) before
+    // exit; only the latest phase of each slot can be waited on
+    for (uint32_t q = q_issued > (uint32_t)S ? q_issued - S : 0; q < q_issued; ++q)
+      mbar_wait(&full[q % S], (q / S) & 1u, kWaitNs);
+  }
+}
+
+template <typename T, bool OPT>
+void set_smem_attr() {
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute((const void*)k_refine<T, OPT>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    done = true;
+  }
 }
 
 }  // namespace
 
-int launch_refine(const FieldDev* fds, const double* const* times, const double* t_ref,
-                  const double* grid, int storage, bool optimise, const float* theta,
-                  const int32_t* centre, const int32_t* field, const st_candidate* cand,
-                  int64_t n, int steps, float fwhm, float lr_pos, float lr_vel, float* J,
-                  float* snr, float* grad, st_refined* out, cudaStream_t s) {
+int refine_max_frames() { return 8192; }
+
+int launch_refine(const FieldDev* h_fds, int n_fields, const FieldDev* fds, CUtensorMap* d_maps,
+                  const double* const* times, const double* t_ref, const double* grid,
+                  int storage, bool optimise, const float* theta, const int32_t* centre,
+                  const int32_t* field, const st_candidate* cand, int64_t n, int steps,
+                  float fwhm, float lr_pos, float lr_vel, float* J, float* snr, float* grad,
+                  st_refined* out, int* err, cudaStream_t s) {
   if (n <= 0) return 0;
+  // tensor maps of the fields' cubes (box: the footprint of one frame)
+  std::vector<CUtensorMap> maps(n_fields);
+  int max_n = 0;
+  for (int f = 0; f < n_fields; ++f) {
+    if (!encode_tile_map(&maps[f], h_fds[f], kBoxW, kBoxH)) return -1;
+    max_n = h_fds[f].N > max_n ? h_fds[f].N : max_n;
+  }
+  if (max_n > refine_max_frames()) return -1;
+  if (cudaMemcpyAsync(d_maps, maps.data(), sizeof(CUtensorMap) * n_fields,
+                      cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return -1;
   RefineArgs a{};
   a.fds = fds;
+  a.maps = d_maps;
   a.times = times;
   a.t_ref = t_ref;
   a.theta_in = theta;
@@ -254,7 +367,14 @@ int launch_refine(const FieldDev* fds, const double* const* times, const double*
   a.snr = snr;
   a.grad = grad;
   a.out = out;
-#define ST_REF(T, O) k_refine<T, O><<<(unsigned)n, kThreads, 0, s>>>(a)
+  a.err = err;
+  const size_t dt_bytes = sizeof(float) * (size_t)max_n;
+#define ST_REF(T, O)                                                                         \
+  do {                                                                                       \
+    set_smem_attr<T, O>();                                                                   \
+    const size_t smem = (size_t)stages_for<T>() * box_bytes<T>() + dt_bytes + 128;           \
+    k_refine<T, O><<<(unsigned)n, kThreads, smem, s>>>(a);                                   \
+  } while (0)
   if (storage == ST_F32) {
     if (optimise) ST_REF(float, true); else ST_REF(float, false);
   } else if (storage == ST_F16) {

@@ -748,6 +748,23 @@ struct FastPlan {
 
 int fast_plan_size_bytes() { return (int)sizeof(FastPlan); }
 
+bool encode_tile_map(CUtensorMap* map, const FieldDev& fd, int box_w, int box_h) {
+  if (!encode_fn()) return false;
+  const int esz = fd.storage == ST_F32 ? 4 : 2;
+  const CUtensorMapDataType dtype = fd.storage == ST_F32    ? Store<float>::kTma
+                                    : fd.storage == ST_F16 ? Store<__half>::kTma
+                                                           : Store<__nv_bfloat16>::kTma;
+  if (((int64_t)fd.W * esz) % 16 != 0) return false;  // row pitch: a multiple of 16 bytes
+  cuuint64_t dims[3] = {(cuuint64_t)fd.W, (cuuint64_t)fd.H, (cuuint64_t)fd.N};
+  cuuint64_t strides[2] = {(cuuint64_t)fd.W * esz, (cuuint64_t)fd.W * fd.H * esz};
+  cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return encode_fn()(map, dtype, 3, const_cast<void*>(fd.cube), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int fast_num_variants() { return kNumVariants; }
 
 int fast_num_variants_for(const FastPlan* fp, int storage) {

@@ -95,6 +95,8 @@ struct st_plan_s {
   double** d_times = nullptr;  // per field: device pointer to its timestamps
   double* d_tref = nullptr;    // per field
   double* d_grid = nullptr;    // per field: vx0, dvx, vy0, dvy
+  CUtensorMap* d_maps = nullptr;  // per field: TMA map of the cube for the refinement
+  int* d_rerr = nullptr;          // refinement timeout flag
   double* d_sky = nullptr;
   st_candidate* d_hout = nullptr;
   int64_t hout_cap = 0;
@@ -126,6 +128,8 @@ void free_plan(st_plan_t* p) {
   }
   cudaFree(p->d_pend);
   cudaFree(p->d_ctr);
+  cudaFree(p->d_maps);
+  cudaFree(p->d_rerr);
   if (p->h_ctr) cudaFreeHost(p->h_ctr);
   cudaFree(p->d_cand);
   cudaFree(p->d_keys);
@@ -348,6 +352,31 @@ st_status device_search(st_plan_t* p, const float* const* d_frames, const double
   return ST_OK;
 }
 
+// The refinement kernel over the fields' cubes of the last search.
+st_status run_refine(st_plan_t* p, bool optimise, const float* theta, const int32_t* centre,
+                     const int32_t* field, const st_candidate* cand, int64_t n, int steps,
+                     float fwhm, float lr_pos, float lr_vel, float* J, float* snr, float* grad,
+                     st_refined* out) {
+  const int nf = (int)p->F.size();
+  std::vector<FieldDev> h(nf);
+  for (int fi = 0; fi < nf; ++fi)
+    h[fi] = field_dev(p->F[fi], p->F[fi].last_frames, fi, p->o.storage);
+  CK(cudaMemsetAsync(p->d_rerr, 0, sizeof(int), p->s));
+  int l = launch_refine(h.data(), nf, p->d_fds, p->d_maps, p->d_times, p->d_tref, p->d_grid,
+                        h[0].storage, optimise, theta, centre, field, cand, n, steps, fwhm,
+                        lr_pos, lr_vel, J, snr, grad, out, p->d_rerr, p->s);
+  if (l < 0)
+    return fail(ST_ERR_UNSUPPORTED, "refinement needs frame rows of a multiple of 16 bytes "
+                "and at most %d frames per field", refine_max_frames());
+  CK(cudaGetLastError());
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, p->d_rerr, sizeof(int), cudaMemcpyDeviceToHost, p->s));
+  CK(cudaStreamSynchronize(p->s));
+  p->launches = l;
+  if (herr) return fail(ST_ERR_TIMEOUT, "refinement: a frame copy did not land within 2 s");
+  return ST_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -441,6 +470,8 @@ st_status st_plan(const st_field* fields, int32_t n_fields, const st_opts* opts,
     guard(cudaMalloc(&p->d_times, sizeof(double*) * n_fields), "cudaMalloc(times)");
     guard(cudaMalloc(&p->d_tref, sizeof(double) * n_fields), "cudaMalloc(tref)");
     guard(cudaMalloc(&p->d_grid, sizeof(double) * 4 * n_fields), "cudaMalloc(grid)");
+    guard(cudaMalloc(&p->d_maps, sizeof(CUtensorMap) * n_fields), "cudaMalloc(maps)");
+    guard(cudaMalloc(&p->d_rerr, sizeof(int)), "cudaMalloc(rerr)");
     if (st == ST_OK) {
       std::vector<double*> tp(n_fields);
       std::vector<double> tr(n_fields), gr(4 * n_fields);
@@ -621,14 +652,8 @@ st_status st_refine(st_plan_t* p, const st_candidate* d_in, int64_t n, int32_t s
   if (optimizer != 0) return fail(ST_ERR_UNSUPPORTED, "only optimizer 0 (Adam) is built");
   if (!p->has_search) return fail(ST_ERR_INVALID, "st_refine needs a prior st_stack_search");
   if (n == 0) return ST_OK;
-  int storage = (p->F[0].d_cube ? p->o.storage : ST_F32);
-  launch_refine(p->d_fds, p->d_times, p->d_tref, p->d_grid, storage, true, nullptr, nullptr,
-                nullptr, d_in, n, steps, fwhm, lr_pos, lr_vel, nullptr, nullptr, d_grad_out,
-                d_out, p->s);
-  CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(p->s));
-  p->launches = 1;
-  return ST_OK;
+  return run_refine(p, true, nullptr, nullptr, nullptr, d_in, n, steps, fwhm, lr_pos, lr_vel,
+                    nullptr, nullptr, d_grad_out, d_out);
 }
 
 st_status st_refine_eval(st_plan_t* p, const float* d_theta, const int32_t* d_centre,
@@ -640,12 +665,8 @@ st_status st_refine_eval(st_plan_t* p, const float* d_theta, const int32_t* d_ce
   if (!(fwhm > 0.0f) || !std::isfinite(fwhm)) return fail(ST_ERR_INVALID, "fwhm must be > 0");
   if (!p->has_search) return fail(ST_ERR_INVALID, "st_refine_eval needs a prior st_stack_search");
   if (n == 0) return ST_OK;
-  int storage = (p->F[0].d_cube ? p->o.storage : ST_F32);
-  launch_refine(p->d_fds, p->d_times, p->d_tref, p->d_grid, storage, false, d_theta, d_centre,
-                d_field, nullptr, n, 0, fwhm, 0.0f, 0.0f, d_J, d_snr, d_grad, nullptr, p->s);
-  CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(p->s));
-  return ST_OK;
+  return run_refine(p, false, d_theta, d_centre, d_field, nullptr, n, 0, fwhm, 0.0f, 0.0f, d_J,
+                    d_snr, d_grad, nullptr);
 }
 
 }  // extern "C"

@@ -2,6 +2,7 @@
 // host).  Not part of the C ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -113,10 +114,20 @@ int launch_pad_keys(uint64_t* keys, uint32_t* idx, int64_t n_pow2, const Counter
 // the given theta; optimise == true runs `steps` Adam steps from each
 // candidate's grid velocity and pixel, with F at its optimum, and writes the
 // refined records.
-int launch_refine(const FieldDev* fds, const double* const* times, const double* t_ref,
-                  const double* grid, int storage, bool optimise, const float* theta,
-                  const int32_t* centre, const int32_t* field, const st_candidate* cand,
-                  int64_t n, int steps, float fwhm, float lr_pos, float lr_vel, float* J,
-                  float* snr, float* grad, st_refined* out, cudaStream_t s);
+// Refinement (forward + adjoint, optional Adam steps) of n candidates; h_fds
+// are the host copies of the n_fields device descriptors fds (their cubes are
+// mapped for TMA into d_maps, n_fields entries).  Returns -1 if a field cannot
+// be mapped or has more than refine_max_frames() frames.
+int refine_max_frames();
+int launch_refine(const FieldDev* h_fds, int n_fields, const FieldDev* fds, CUtensorMap* d_maps,
+                  const double* const* times, const double* t_ref, const double* grid,
+                  int storage, bool optimise, const float* theta, const int32_t* centre,
+                  const int32_t* field, const st_candidate* cand, int64_t n, int steps,
+                  float fwhm, float lr_pos, float lr_vel, float* J, float* snr, float* grad,
+                  st_refined* out, int* err, cudaStream_t s);
+
+// Tiled TMA map of a field's cube [N][H][W] (storage type) with a box of
+// box_w x box_h x 1 elements, zero fill outside.  False if it cannot be built.
+bool encode_tile_map(CUtensorMap* map, const FieldDev& fd, int box_w, int box_h);
 
 }  // namespace st

@@ -69,6 +69,36 @@ def test_refine_eval_matches_oracle(st):
     assert np.all(np.abs(g - og) <= 2e-4 * scale), np.abs(g - og).max()
 
 
+def test_refine_eval_edges_and_interior(st):
+    # cutouts hanging over each border and corner (zero taps outside) and
+    # cutouts whose every frame footprint is inside (the unchecked-load path)
+    fr, t, f = make(seed=45, W=256, H=200)
+    rng = np.random.default_rng(5)
+    dt = t - f["t_ref"]
+    cen = [(3, 100), (252, 100), (128, 2), (128, 198), (0, 0), (255, 199), (128, 100),
+           (100, 90), (150, 110)]
+    th, ce = [], []
+    for cx, cy in cen:
+        while True:
+            vx, vy = rng.uniform(-0.9, 0.9, 2)
+            if kink_free(vx, dt) and kink_free(vy, dt):
+                break
+        th.append([vx, vy, cx + rng.uniform(-0.5, 0.5), cy + rng.uniform(-0.5, 0.5), 1.5])
+        ce.append([cx, cy])
+    th = np.array(th)
+    ce = np.array(ce, np.int32)
+    with st.Plan(f) as p:
+        p.candidates(torch.from_numpy(fr).cuda(), t)
+        J, snr, g = p.refine_eval(torch.tensor(th, dtype=torch.float32).cuda(), ce)
+    oJ, osnr, og = oracle.refine_eval(fr, t, f["t_ref"], th.astype(np.float32).astype(np.float64),
+                                      ce)
+    J, snr, g = J.cpu().numpy(), snr.cpu().numpy(), g.cpu().numpy()
+    scale = np.abs(og).max(axis=1, keepdims=True) + 1.0
+    assert np.all(np.abs(J - oJ) <= 2e-4 * (np.abs(oJ) + 1.0))
+    assert np.all(np.abs(snr - osnr) <= 2e-4 * (np.abs(osnr) + 1.0))
+    assert np.all(np.abs(g - og) <= 2e-4 * scale), np.abs(g - og).max()
+
+
 def test_autograd_backward_is_the_adjoint(st):
     fr, t, f = make(seed=43)
     th = torch.tensor([[0.37, -0.23, 80.4, 74.3, 2.2]], dtype=torch.float32, device="cuda",
