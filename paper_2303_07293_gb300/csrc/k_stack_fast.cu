@@ -37,6 +37,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <climits>
 #include <cstring>
 #include <new>
@@ -79,22 +80,14 @@ struct Store<__nv_bfloat16> {
 constexpr int kSuper = 4;        // pixel tiles per super-tile side (L2 locality)
 constexpr uint64_t kWaitNs = 2000000000ull;  // wait limit: 2 s of wall-clock time
 constexpr unsigned kProducerSleepNs = 128;  // producer back-off between polls
-constexpr int kParamBytes = 28672;  // staircase pattern ids carried in the kernel parameters
 constexpr int kPatterns = 15;
 
-struct FastArgs {
-  int W, H, N, nvx, nvy, nA, nB, stage_floats;
-  int ty_rows;      // tile height (rows per thread of the variant)
-  int B0, G;        // this launch covers y-velocity groups B0 .. B0+G-1
-  int64_t n_items;  // work items of this launch
-  int tiles_x, tiles_y, super_x, super_y;
-  int nmin, field;
+// One field of a launch: geometry, per-frame tile tables and thresholds.
+struct FastField {
+  int W, H, N, nvx, nvy, nA, nB, nmin, field;
   const int4* xt;   // [N][nA]: box x offset, packed 4-bit column offsets, min shift, max shift
   const int4* yt;   // [N][nB]: min shift, max shift, pattern id, 0
-  const int* xmin;  // [nA] min over frames of the min shift
-  const int* xmax;  // [nA] max over frames of the max shift
-  const int* ymin;  // [nB]
-  const int* ymax;  // [nB]
+  const unsigned char* pat;  // [N][nB] staircase pattern ids
   const int32_t* sx;
   const int32_t* sy;
   const float* fx;   // bilinear: FP32 fractions [N][nvx], [N][nvy]
@@ -111,14 +104,21 @@ struct FastArgs {
   const int* cov_ymin;
   const int* cov_ymax;
   int cov_len;
+};
+
+constexpr int kMaxFields = 256;
+
+struct FastArgs {
+  const FastField* ff[kMaxFields];    // the launch's fields, longest first (device)
+  const CUtensorMap* maps[kMaxFields];  // their cubes' tiled maps (global memory)
+  int n_fields;
+  int64_t n_items;            // items of all fields
+  unsigned long long* work;   // next item to take (zero at launch)
   Pending* pend;
   int64_t cap;
   Counters* ctr;
-  float* dump_S;    // optional [nvx*nvy][H][W] (tests)
+  float* dump_S;    // optional [nvx*nvy][H][W] of a single field (tests)
   int32_t* dump_C;
-  // [G][N] staircase pattern ids.  Parameter-space loads are uniform, so the
-  // per-frame switch is a uniform branch.
-  unsigned char pat[kParamBytes];
 };
 
 // Pattern id -> row offsets of the 4 y-velocities (min offset 0).
@@ -286,7 +286,7 @@ __device__ __forceinline__ int count_shifts(const int* pre, int smin, int smax, 
   return hi < lo ? 0 : upto(hi) - upto(lo - 1);
 }
 
-__device__ int exact_coverage(const FastArgs& p, int x, int y, int av, int bv) {
+__device__ int exact_coverage(const FastField& p, int x, int y, int av, int bv) {
   int c = 0;
   for (int i = 0; i < p.N; ++i) {
     int u = x + __ldg(p.sx + (int64_t)i * p.nvx + av);
@@ -296,7 +296,7 @@ __device__ int exact_coverage(const FastArgs& p, int x, int y, int av, int bv) {
   return c;
 }
 
-__device__ int exact_coverage_bl(const FastArgs& p, int x, int y, int av, int bv) {
+__device__ int exact_coverage_bl(const FastField& p, int x, int y, int av, int bv) {
   int c = 0;
   for (int i = 0; i < p.N; ++i) {
     int u = x + __ldg(p.sx + (int64_t)i * p.nvx + av);
@@ -307,41 +307,58 @@ __device__ int exact_coverage_bl(const FastArgs& p, int x, int y, int av, int bv
   return c;
 }
 
-// Work item -> tile and velocity tile.  Items are ordered (super-tile,
-// velocity tile, sub-tile) with the sub-tile fastest, so consecutive items
-// (which neighbouring CTAs run at the same time) share most of their frame
-// footprints in L2.
+// Work item -> field, tile and velocity tile.  A field's items are ordered
+// (super-tile, velocity tile, sub-tile) with the sub-tile fastest, so
+// consecutive items (which neighbouring CTAs run at the same time) share most
+// of their frame footprints in L2.  Fields are numbered longest first (most
+// frames), so the short items of the last fields fill the tail.
 struct Item {
-  int X0, Y0, A, g, B;
+  int f;           // index into the launch's field list (-1: no more work)
+  int X0, Y0, A, B;
 };
-__device__ __forceinline__ Item decode_item(const FastArgs& p, int64_t L) {
-  const int nVT = p.nA * p.G;
+// Items of a field for tile height ky: super-tiles x 16 tiles x velocity tiles.
+__device__ __host__ __forceinline__ int super_x_of(int W) { return ((W + kTX - 1) / kTX + kSuper - 1) / kSuper; }
+__device__ __host__ __forceinline__ int64_t items_of(const FastField& ff, int ky) {
+  const int sy = ((ff.H + ky - 1) / ky + kSuper - 1) / kSuper;
+  return (int64_t)super_x_of(ff.W) * sy * kSuper * kSuper * ff.nA * ff.nB;
+}
+__device__ __forceinline__ Item decode_item(const FastField& ff, int f, int64_t L, int ky) {
+  const int nVT = ff.nA * ff.nB;
+  const int super_x = super_x_of(ff.W);
   const int sub = (int)(L % (kSuper * kSuper));
   const int64_t rest = L / (kSuper * kSuper);
   const int vt = (int)(rest % nVT);
   const int stile = (int)(rest / nVT);
   Item it;
-  it.X0 = ((stile % p.super_x) * kSuper + sub % kSuper) * kTX;
-  it.Y0 = ((stile / p.super_x) * kSuper + sub / kSuper) * p.ty_rows;
-  it.A = vt % p.nA;
-  it.g = vt / p.nA;
-  it.B = p.B0 + it.g;
+  it.f = f;
+  it.X0 = ((stile % super_x) * kSuper + sub % kSuper) * kTX;
+  it.Y0 = ((stile / super_x) * kSuper + sub / kSuper) * ky;
+  it.A = vt % ff.nA;
+  it.B = vt / ff.nA;
   return it;
 }
 
-// Persistent kernel (BL: bilinear sampling): every CTA walks the items blockIdx.x, blockIdx.x +
-// gridDim.x, ...  Each item's frames are padded to whole stages of F frames
-// (padding frames are no-ops with no copy).  Warp 8 is the producer: it runs
-// ahead in stages, its lanes fetch the per-frame table entries and issue the
-// TMA copies of a stage in parallel, and it publishes the frames' column
-// offsets and each item's count of fully-inside frames in shared memory.
-// Warps 0..7 consume; the pattern id of a frame comes from the kernel
-// parameters through a warp-uniform index, so its switch is a uniform
-// branch.  A ring of S stages runs continuously across items.  Every wait is
-// bounded in time.
+// Acquire a tensor map written to global memory before the launch for the
+// TMA unit (tensor-map proxy).
+__device__ __forceinline__ void tmap_acquire(const CUtensorMap* m) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)m)
+               : "memory");
+}
+
+// Persistent kernel over every item of every field of the launch (BL:
+// bilinear sampling).  Warp 8 is the producer: it takes the next item from
+// the launch's work counter (dynamic, in the fields' longest-first order),
+// publishes the item in a ring of kItemSlots shared-memory slots, and runs
+// ahead in stages of F frames (an item's frames are padded to whole stages
+// with no-op frames, which have no copy): its lanes fetch the per-frame table
+// entries, issue the TMA copies of a stage in parallel and publish the
+// frames' column offsets, pattern ids (and bilinear fractions) and each
+// item's count of fully-inside frames in shared memory.  Warps 0..7 consume.
+// A ring of S stages runs continuously across items and fields; when the
+// work runs out the producer publishes an end item.  Every wait is bounded.
 template <typename T, int KY, int S, int F, bool DUMP, bool BL>
 __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
-    k_stack_fast(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ FastArgs p) {
+    k_stack_fast(const __grid_constant__ FastArgs p) {
   constexpr int kBoxW = Store<T>::kBoxW;
   constexpr int kTY = KY;         // tile height: one row group of KY rows per thread
   constexpr int kBoxH = KY + 3 + (BL ? 1 : 0);  // tile rows + staircase offset (+ lower tap)
@@ -355,9 +372,12 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
   __shared__ __align__(8) uint64_t full_bar[S];
   __shared__ __align__(8) uint64_t empty_bar[S];
   __shared__ uint32_t slot_ocol[S * F];     // packed 4-bit column offsets of the 8 warps
+  __shared__ uint32_t slot_ids[S];          // packed 8-bit pattern ids of the stage's frames
   __shared__ float slot_fx[BL ? S * F * kXV : 1];  // bilinear: x-fraction of each warp
   __shared__ float4 slot_fy[BL ? S * F : 1];       // bilinear: y-fractions of the 4 y-velocities
   __shared__ int item_inside[kItemSlots];   // frames of an item fully inside the frame
+  __shared__ int item_done[kItemSlots];     // consumer warps done with an item
+  __shared__ Item item_info[kItemSlots];    // the items in flight
 
   T* smem = reinterpret_cast<T*>(reinterpret_cast<char*>(smem_raw) +
                                  ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
@@ -365,72 +385,103 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
   const uint32_t box_bytes = (uint32_t)kBoxH * kBoxW * sizeof(T);
   // one frame's box in elements, padded to 128 bytes (compile-time stride)
   constexpr int box_floats = ((kBoxH * kBoxW * (int)sizeof(T) + 127) & ~127) / (int)sizeof(T);
-  const int N = p.N;
-  const int spi = (N + F - 1) / F;       // stages per item
-  const int G = (int)gridDim.x;
-  const int my_items =
-      (int)blockIdx.x < p.n_items ? (int)((p.n_items - blockIdx.x + G - 1) / G) : 0;
-  const int n_stages = my_items * spi;
 
   if (tid == 0) {
-    tma_prefetch_desc(&tmap);
     for (int s = 0; s < S; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], kCW);
     }
     mbar_init_fence();
   }
-  if (tid < kItemSlots) item_inside[tid] = 0;
+  if (tid < kItemSlots) {
+    item_inside[tid] = 0;
+    item_done[tid] = 0;
+  }
   __syncthreads();
 
   if (warp == kXV) {
     // ------------------------------------------------------------ producer
-    int slot = 0, item = 0, st = 0;
-    Item it = decode_item(p, blockIdx.x);
-    for (int seq = 0; seq < n_stages; ++seq) {
-      if (seq >= S && !mbar_wait_sleep(&empty_bar[slot], (uint32_t)(seq / S - 1) & 1u, kWaitNs,
-                                        kProducerSleepNs)) {
-        if (lane == 0) atomicOr(&p.ctr->error, ERR_TIMEOUT);
-        break;  // consumers time out on the missing stage (bounded)
+    int slot = 0, f = 0, acq_f = -1;
+    int64_t base = 0;                        // first item of field f
+    int64_t f_items = items_of(*p.ff[0], KY);  // items of field f
+    int64_t seq = 0;  // stages issued
+    bool ok = true;
+    for (int item = 0; ok; ++item) {
+      int64_t L = 0;
+      if (lane == 0) L = (int64_t)atomicAdd(p.work, 1ull);
+      L = __shfl_sync(0xffffffffu, L, 0);
+      const bool done = L >= p.n_items;
+      // the field of item L (items are taken in increasing order)
+      while (!done && L >= base + f_items) {
+        base += f_items;
+        f_items = items_of(*p.ff[++f], KY);
       }
-      const int nbox = min(F, N - st * F);  // real frames in this stage
-      if (lane == 0) mbar_expect_tx(&full_bar[slot], box_bytes * (uint32_t)nbox);
-      if (lane < nbox) {
-        const int fr = st * F + lane;
-        const int4 xe = __ldg(p.xt + (int64_t)fr * p.nA + it.A);
-        const int4 ye = __ldg(p.yt + (int64_t)fr * p.nB + it.B);
-        slot_ocol[slot * F + lane] = (uint32_t)xe.y;
-        if constexpr (BL) {
-          const float4 f0 = __ldg(p.fxt + 2 * ((int64_t)fr * p.nA + it.A));
-          const float4 f1 = __ldg(p.fxt + 2 * ((int64_t)fr * p.nA + it.A) + 1);
-          float* d = slot_fx + (slot * F + lane) * kXV;
-          d[0] = f0.x; d[1] = f0.y; d[2] = f0.z; d[3] = f0.w;
-          d[4] = f1.x; d[5] = f1.y; d[6] = f1.z; d[7] = f1.w;
-          slot_fy[slot * F + lane] = __ldg(p.fyt + (int64_t)fr * p.nB + it.B);
+      const FastField& ff = *p.ff[f];
+      Item it{-1, 0, 0, 0, 0};
+      if (!done) it = decode_item(ff, f, L - base, KY);
+      const CUtensorMap* map = p.maps[f];
+      if (!done && f != acq_f) {
+        if (lane == 0) {
+          tmap_acquire(map);
+          tma_prefetch_desc(map);
         }
-        // every sample of the item strictly inside (bilinear: with its right
-        // and lower taps), so every output of the item is covered by frame fr
-        const bool inside = it.X0 + xe.z >= 0 && it.X0 + kTX - 1 + xe.w + kEdge < p.W &&
-                            it.Y0 + ye.x >= 0 && it.Y0 + kTY - 1 + ye.y + kEdge < p.H;
-        if (inside) atomicAdd(&item_inside[item % kItemSlots], 1);
-        tma_load_3d(smem + (size_t)(slot * F + lane) * box_floats, &tmap, it.X0 + xe.x,
-                    it.Y0 + ye.x, fr, &full_bar[slot]);
+        acq_f = f;
+      }
+      const int N = done ? 1 : ff.N;
+      const int spi = (N + F - 1) / F;  // stages of this item (an end item: one)
+      for (int st = 0; st < spi; ++st, ++seq) {
+        if (seq >= S &&
+            !mbar_wait_sleep(&empty_bar[slot], (uint32_t)(seq / S - 1) & 1u, kWaitNs,
+                             kProducerSleepNs)) {
+          if (lane == 0) atomicOr(&p.ctr->error, ERR_TIMEOUT);
+          ok = false;
+          break;  // consumers time out on the missing stage (bounded)
+        }
+        if (st == 0 && lane == 0) item_info[item % kItemSlots] = it;
+        const int nbox = done ? 0 : min(F, N - st * F);  // real frames in this stage
+        if (lane == 0 && nbox > 0) mbar_expect_tx(&full_bar[slot], box_bytes * (uint32_t)nbox);
+        unsigned id = kNoop;  // padding frames (and bytes past F) are no-ops
+        {
+          if (lane < nbox) {
+            const int fr = st * F + lane;
+            const int4 xe = __ldg(ff.xt + (int64_t)fr * ff.nA + it.A);
+            const int4 ye = __ldg(ff.yt + (int64_t)fr * ff.nB + it.B);
+            id = ff.pat[(int64_t)fr * ff.nB + it.B];
+            slot_ocol[slot * F + lane] = (uint32_t)xe.y;
+            if constexpr (BL) {
+              const float4 f0 = __ldg(ff.fxt + 2 * ((int64_t)fr * ff.nA + it.A));
+              const float4 f1 = __ldg(ff.fxt + 2 * ((int64_t)fr * ff.nA + it.A) + 1);
+              float* d = slot_fx + (slot * F + lane) * kXV;
+              d[0] = f0.x; d[1] = f0.y; d[2] = f0.z; d[3] = f0.w;
+              d[4] = f1.x; d[5] = f1.y; d[6] = f1.z; d[7] = f1.w;
+              slot_fy[slot * F + lane] = __ldg(ff.fyt + (int64_t)fr * ff.nB + it.B);
+            }
+            // every sample of the item strictly inside (bilinear: with its
+            // right and lower taps), so every output of the item is covered
+            const bool inside = it.X0 + xe.z >= 0 && it.X0 + kTX - 1 + xe.w + kEdge < ff.W &&
+                                it.Y0 + ye.x >= 0 && it.Y0 + kTY - 1 + ye.y + kEdge < ff.H;
+            if (inside) atomicAdd(&item_inside[item % kItemSlots], 1);
+            tma_load_3d(smem + (size_t)(slot * F + lane) * box_floats, map, it.X0 + xe.x,
+                        it.Y0 + ye.x, fr, &full_bar[slot]);
+          }
+        }
+        // the stage's ids, packed: lane l's id in byte l
+        uint32_t w = lane < 4 ? id << (8 * lane) : 0u;
+        w |= __shfl_xor_sync(0xffffffffu, w, 1);
+        w |= __shfl_xor_sync(0xffffffffu, w, 2);
+        if (lane == 0) slot_ids[slot] = w;
         __threadfence_block();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&full_bar[slot]);  // releases this stage's info
+        if (++slot == S) slot = 0;
       }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&full_bar[slot]);  // releases this stage's info
-      if (++slot == S) slot = 0;
-      if (++st == spi) {
-        st = 0;
-        ++item;
-        if (item < my_items) it = decode_item(p, blockIdx.x + (int64_t)item * G);
-      }
+      if (done) break;
     }
     // drain (matters only after a consumer timeout): the last use of each
     // ring slot completes before the CTA may exit.  Only the latest phase of a
     // slot can be waited on: an older phase's parity aliases a newer one.
     if (lane == 0) {
-      for (int sq = n_stages > S ? n_stages - S : 0; sq < n_stages; ++sq)
+      for (int64_t sq = seq > S ? seq - S : 0; sq < seq; ++sq)
         mbar_wait(&full_bar[sq % S], (uint32_t)(sq / S) & 1u, kWaitNs);
     }
     return;
@@ -440,32 +491,31 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
   const int xw = warp;
   int c_slot = 0;
   uint32_t c_ph = 0;
-  bool ok = true;
-  for (int item = 0; item < my_items && ok; ++item) {
-    // uniform; only the pattern row stays live through the frame loop.  The
-    // row is padded to spi * F entries with no-op ids.
-    const unsigned char* pat =
-        p.pat + decode_item(p, blockIdx.x + (int64_t)item * G).g * (spi * F);
+  for (int item = 0;; ++item) {
+    // the item's first stage carries its description
+    if (!__all_sync(0xffffffffu, mbar_wait(&full_bar[c_slot], c_ph, kWaitNs))) {
+      if (lane == 0) atomicOr(&p.ctr->error, ERR_TIMEOUT);  // leave (warp-uniform)
+      break;
+    }
+    const Item it = item_info[item % kItemSlots];
+    if (it.f < 0) break;  // end of the work
+    const FastField& ff = *p.ff[it.f];
+    const int N = ff.N;
+    const int spi = (N + F - 1) / F;
     float2 acc[kMB][KY / 2];
 #pragma unroll
     for (int j = 0; j < kMB; ++j)
 #pragma unroll
       for (int m = 0; m < KY / 2; ++m) acc[j][m] = make_float2(0.0f, 0.0f);
 
+    bool ok = true;
     for (int st = 0; st < spi; ++st) {
-      if (!__all_sync(0xffffffffu, mbar_wait(&full_bar[c_slot], c_ph, kWaitNs))) {
-        if (lane == 0) atomicOr(&p.ctr->error, ERR_TIMEOUT);  // leave (warp-uniform)
+      if (st > 0 && !__all_sync(0xffffffffu, mbar_wait(&full_bar[c_slot], c_ph, kWaitNs))) {
+        if (lane == 0) atomicOr(&p.ctr->error, ERR_TIMEOUT);
         ok = false;
         break;
       }
-      // the stage's pattern ids: one packed word per stage (F <= 4)
-      uint32_t idw = 0;
-      if constexpr (F == 4) {
-        idw = *reinterpret_cast<const uint32_t*>(pat + st * F);  // rows padded to 4 bytes
-      } else {
-#pragma unroll
-        for (int fi = 0; fi < F; ++fi) idw |= (uint32_t)pat[st * F + fi] << (8 * fi);
-      }
+      const uint32_t idw = slot_ids[c_slot];  // the stage's pattern ids
       const T* stage = smem + (size_t)(c_slot * F) * box_floats + lane;
       uint32_t oc_next = slot_ocol[c_slot * F];
 #pragma unroll 1
@@ -509,32 +559,32 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
             default: __builtin_unreachable();
           }
         } else {
-        float w[KY + 3];
+          float w[KY + 3];
 #pragma unroll
-        for (int r = 0; r < KY + 3; ++r) w[r] = Store<T>::f(col[r * kBoxW]);
-        if (fi == F - 1) {
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&empty_bar[c_slot]);
-        }
-        switch (id) {
-          case 0: add_pattern<KY, 0>(acc, w); break;
-          case 1: add_pattern<KY, 1>(acc, w); break;
-          case 2: add_pattern<KY, 2>(acc, w); break;
-          case 3: add_pattern<KY, 3>(acc, w); break;
-          case 4: add_pattern<KY, 4>(acc, w); break;
-          case 5: add_pattern<KY, 5>(acc, w); break;
-          case 6: add_pattern<KY, 6>(acc, w); break;
-          case 7: add_pattern<KY, 7>(acc, w); break;
-          case 8: add_pattern<KY, 8>(acc, w); break;
-          case 9: add_pattern<KY, 9>(acc, w); break;
-          case 10: add_pattern<KY, 10>(acc, w); break;
-          case 11: add_pattern<KY, 11>(acc, w); break;
-          case 12: add_pattern<KY, 12>(acc, w); break;
-          case 13: add_pattern<KY, 13>(acc, w); break;
-          case 14: add_pattern<KY, 14>(acc, w); break;
-          case kNoop: break;  // padding frame
-          default: __builtin_unreachable();
-        }
+          for (int r = 0; r < KY + 3; ++r) w[r] = Store<T>::f(col[r * kBoxW]);
+          if (fi == F - 1) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty_bar[c_slot]);
+          }
+          switch (id) {
+            case 0: add_pattern<KY, 0>(acc, w); break;
+            case 1: add_pattern<KY, 1>(acc, w); break;
+            case 2: add_pattern<KY, 2>(acc, w); break;
+            case 3: add_pattern<KY, 3>(acc, w); break;
+            case 4: add_pattern<KY, 4>(acc, w); break;
+            case 5: add_pattern<KY, 5>(acc, w); break;
+            case 6: add_pattern<KY, 6>(acc, w); break;
+            case 7: add_pattern<KY, 7>(acc, w); break;
+            case 8: add_pattern<KY, 8>(acc, w); break;
+            case 9: add_pattern<KY, 9>(acc, w); break;
+            case 10: add_pattern<KY, 10>(acc, w); break;
+            case 11: add_pattern<KY, 11>(acc, w); break;
+            case 12: add_pattern<KY, 12>(acc, w); break;
+            case 13: add_pattern<KY, 13>(acc, w); break;
+            case 14: add_pattern<KY, 14>(acc, w); break;
+            case kNoop: break;  // padding frame
+            default: __builtin_unreachable();
+          }
         }
       }
       if (++c_slot == S) {
@@ -547,7 +597,6 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
     // ---- epilogue of the item (its last stage was waited on, so the
     // producer's count is visible)
     const int n_full = item_inside[item % kItemSlots];
-    const Item it = decode_item(p, blockIdx.x + (int64_t)item * G);
     const int x = it.X0 + lane;
     const int av = it.A * kXV + xw;
     if constexpr (DUMP) {
@@ -558,13 +607,13 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int bv = it.B * kMB + j, y = it.Y0 + 2 * m + h;
-            if (x < p.W && y < p.H && av < p.nvx && bv < p.nvy) {
+            if (x < ff.W && y < ff.H && av < ff.nvx && bv < ff.nvy) {
               const int64_t o =
-                  ((int64_t)bv * p.nvx + av) * p.W * (int64_t)p.H + (int64_t)y * p.W + x;
+                  ((int64_t)bv * ff.nvx + av) * ff.W * (int64_t)ff.H + (int64_t)y * ff.W + x;
               p.dump_S[o] = h == 0 ? acc[j][m].x : acc[j][m].y;
               if (p.dump_C)
-                p.dump_C[o] = BL ? exact_coverage_bl(p, x, y, av, bv)
-                                 : exact_coverage(p, x, y, av, bv);
+                p.dump_C[o] = BL ? exact_coverage_bl(ff, x, y, av, bv)
+                                 : exact_coverage(ff, x, y, av, bv);
             }
           }
     } else {
@@ -577,7 +626,7 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
       for (int b = 0; b < kWords; ++b) mask[b] = 0u;
       if (n_full == N) {
         // interior item: every output is covered by all N frames
-        const float thr_n = __ldg(p.thr + max(N, p.nmin));
+        const float thr_n = __ldg(ff.thr + max(N, ff.nmin));
 #pragma unroll
         for (int j = 0; j < kMB; ++j)
 #pragma unroll
@@ -590,23 +639,23 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
         // edge item: n_cov >= nx + ny - N, with nx / ny the frames whose x / y
         // sample is inside (bilinear: with its right / lower tap, which
         // implies inside for any fraction; ny taken at the item's least
-        // covered row), and
-        // n_cov >= n_full; thresholds grow with n_cov, so this never drops a
-        // candidate
-        const int avc = min(av, p.nvx - 1);
-        const int nx = count_shifts(p.covx + (int64_t)avc * p.cov_len, __ldg(p.cov_xmin + avc),
-                                    __ldg(p.cov_xmax + avc), N, -x, p.W - 1 - kEdge - x);
+        // covered row), and n_cov >= n_full; thresholds grow with n_cov, so
+        // this never drops a candidate
+        const int avc = min(av, ff.nvx - 1);
+        const int nx = count_shifts(ff.covx + (int64_t)avc * ff.cov_len,
+                                    __ldg(ff.cov_xmin + avc), __ldg(ff.cov_xmax + avc), N, -x,
+                                    ff.W - 1 - kEdge - x);
 #pragma unroll
         for (int j = 0; j < kMB; ++j) {
           // ny minimised over the item's rows (lane l takes row l % KY)
-          const int bvc = min(it.B * kMB + j, p.nvy - 1);
+          const int bvc = min(it.B * kMB + j, ff.nvy - 1);
           const int y = it.Y0 + lane % KY;
-          int ny = count_shifts(p.covy + (int64_t)bvc * p.cov_len, __ldg(p.cov_ymin + bvc),
-                                __ldg(p.cov_ymax + bvc), N, -y, p.H - 1 - kEdge - y);
+          int ny = count_shifts(ff.covy + (int64_t)bvc * ff.cov_len, __ldg(ff.cov_ymin + bvc),
+                                __ldg(ff.cov_ymax + bvc), N, -y, ff.H - 1 - kEdge - y);
 #pragma unroll
           for (int d = 16; d > 0; d >>= 1) ny = min(ny, __shfl_xor_sync(0xffffffffu, ny, d));
-          const int nlo = max(max(n_full, p.nmin), nx + ny - N);
-          const float thr_j = __ldg(p.thr + min(nlo, N));
+          const int nlo = max(max(n_full, ff.nmin), nx + ny - N);
+          const float thr_j = __ldg(ff.thr + min(nlo, N));
 #pragma unroll
           for (int m = 0; m < KY / 2; ++m) {
             const int o = j * KY + 2 * m;
@@ -615,7 +664,7 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
           }
         }
       }
-      const bool col_ok = x < p.W && av < p.nvx;
+      const bool col_ok = x < ff.W && av < ff.nvx;
       for (int b = 0; b < kWords; ++b) {
         uint32_t mk = col_ok ? mask[b] : 0u;
         while (__any_sync(0xffffffffu, mk != 0u)) {
@@ -624,32 +673,36 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
           mk &= has ? mk - 1u : 0u;
           const int o = b * 32 + bit;
           const int j = o / KY, y = it.Y0 + o % KY, bv = it.B * kMB + j;
-          const bool valid = has && y < p.H && bv < p.nvy;
-          Pending rec{x, y, bv * p.nvx + av, p.field, 0.0f, -1};
+          const bool valid = has && y < ff.H && bv < ff.nvy;
+          Pending rec{x, y, bv * ff.nvx + av, ff.field, 0.0f, -1};
           push_pending(valid, rec, p.pend, p.cap, p.ctr);
         }
       }
     }
-    // release the item's count slot (the producer is at most S*F frames, far
-    // fewer than kItemSlots - 1 items, ahead)
+    // release the item's count slot: the last warp to finish the item clears
+    // it (the producer is at most S stages, fewer than kItemSlots - 1 items,
+    // ahead of the slowest warp)
     __syncwarp();
-    if (xw == 0 && lane == 0) atomicExch(&item_inside[item % kItemSlots], 0);
+    if (lane == 0 && atomicAdd(&item_done[item % kItemSlots], 1) == kCW - 1) {
+      item_inside[item % kItemSlots] = 0;
+      item_done[item % kItemSlots] = 0;
+    }
   }
 }
 
 // Compiled variants: (rows per thread, stages, frames per stage), each with
 // and without the stack dump used by the tests.
 struct Variant {
-  void (*fn)(CUtensorMap, FastArgs);
-  void (*dump_fn)(CUtensorMap, FastArgs);
+  void (*fn)(FastArgs);
+  void (*dump_fn)(FastArgs);
   int threads, stages, ky, stages_f;
   const char* name;
 };
 
 #define ST_VARIANT(T, KY, S, F, BL)                                                           \
   {                                                                                           \
-    (void (*)(CUtensorMap, FastArgs))k_stack_fast<T, KY, S, F, false, BL>,                      \
-        (void (*)(CUtensorMap, FastArgs))k_stack_fast<T, KY, S, F, true, BL>, 32 * (kXV + 1),  \
+    (void (*)(FastArgs))k_stack_fast<T, KY, S, F, false, BL>,                                   \
+        (void (*)(FastArgs))k_stack_fast<T, KY, S, F, true, BL>, 32 * (kXV + 1),               \
         S * F, KY, F, #T "_ky" #KY "_s" #S "_f" #F                                             \
   }
 const Variant kVarF32[] = {ST_VARIANT(float, 16, 6, 4, false), ST_VARIANT(float, 16, 8, 4, false),
@@ -734,7 +787,9 @@ struct FastPlan {
   int64_t item_limit = 0;  // > 0: run only the first item_limit items (autotuning)
   int nA = 0, nB = 0, N = 0;
   unsigned char* d_pat = nullptr;  // [N][nB] pattern ids
-  unsigned char* h_pat = nullptr;  // pinned copy for the kernel parameters
+  FastField h_ff{};                // the field's descriptor (host copy)
+  FastField* d_ff = nullptr;       // and on the device
+  CUtensorMap* d_map = nullptr;    // the cube's tiled map on the device (64-byte aligned)
   int4* xt = nullptr;
   int4* yt = nullptr;
   float* fxt = nullptr;   // bilinear: [N][nA][8] x-fractions
@@ -841,7 +896,8 @@ bool fast_plan_build(const FieldDev& fd, int mode, FastPlan** out) {
               cudaMalloc(&fp->ranges, sizeof(int) * (2 * fp->nA + 2 * fp->nB + 3)) == cudaSuccess &&
               cudaMallocHost(&fp->h_maxes, sizeof(int) * 3) == cudaSuccess &&
               cudaMalloc(&fp->d_pat, (size_t)fd.N * fp->nB) == cudaSuccess &&
-              cudaMallocHost(&fp->h_pat, (size_t)fd.N * fp->nB) == cudaSuccess;
+              cudaMalloc(&fp->d_ff, sizeof(FastField)) == cudaSuccess &&
+              cudaMalloc(&fp->d_map, sizeof(CUtensorMap)) == cudaSuccess;
   if (!good) {
     fast_plan_free(fp);
     return false;
@@ -860,7 +916,8 @@ void fast_plan_free(FastPlan* fp) {
   cudaFree(fp->cov);
   if (fp->h_maxes) cudaFreeHost(fp->h_maxes);
   cudaFree(fp->d_pat);
-  if (fp->h_pat) cudaFreeHost(fp->h_pat);
+  cudaFree(fp->d_ff);
+  cudaFree(fp->d_map);
   delete fp;
 }
 
@@ -894,7 +951,6 @@ int fast_prepare(const FieldDev& fd, FastPlan* fp, cudaStream_t s, bool* fits) {
   k_shift_spread<<<(fd.nvx + 127) / 128, 128, 0, s>>>(fd.sx, fd.N, fd.nvx, maxes + 2);
   k_shift_spread<<<(fd.nvy + 127) / 128, 128, 0, s>>>(fd.sy, fd.N, fd.nvy, maxes + 2);
   cudaMemcpyAsync(fp->h_maxes, maxes, sizeof(int) * 3, cudaMemcpyDeviceToHost, s);
-  cudaMemcpyAsync(fp->h_pat, fp->d_pat, (size_t)fd.N * nB, cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return 1;
   // coverage prefix tables: one row per velocity, as long as the widest spread
   const int len = fp->h_maxes[2];
@@ -917,123 +973,122 @@ int fast_prepare(const FieldDev& fd, FastPlan* fp, cudaStream_t s, bool* fits) {
   k_cov_tables<<<(fd.nvx + 127) / 128, 128, 0, s>>>(fd.sx, fd.N, fd.nvx, len, covx, cxmin, cxmax);
   k_cov_tables<<<(fd.nvy + 127) / 128, 128, 0, s>>>(fd.sy, fd.N, fd.nvy, len, covy, cymin, cymax);
   if (cudaGetLastError() != cudaSuccess) return 1;
-  // N >= 8: the producer runs at most S*F = 24 frames ahead of the consumers,
-  // so at most 4 items are live and the 8 per-item slots never collide.
-  // bilinear reads one more column: lane 31 + ocol + 1 must stay in the box
+  // the field's descriptor for the kernel (pageable source: the copy is
+  // staged before cudaMemcpyAsync returns)
+  FastField& h = fp->h_ff;
+  h = FastField{};
+  h.W = fd.W;
+  h.H = fd.H;
+  h.N = fd.N;
+  h.nvx = fd.nvx;
+  h.nvy = fd.nvy;
+  h.nA = nA;
+  h.nB = nB;
+  h.nmin = fd.nmin;
+  h.field = fd.field;
+  h.xt = fp->xt;
+  h.yt = fp->yt;
+  h.pat = fp->d_pat;
+  h.sx = fd.sx;
+  h.sy = fd.sy;
+  h.fx = fd.fx;
+  h.fy = fd.fy;
+  h.fxt = reinterpret_cast<const float4*>(fp->fxt);
+  h.fyt = reinterpret_cast<const float4*>(fp->fyt);
+  h.thr = fd.thr;
+  h.cov_len = len;
+  h.covx = covx;
+  h.covy = covy;
+  h.cov_xmin = cxmin;
+  h.cov_xmax = cxmax;
+  h.cov_ymin = cymin;
+  h.cov_ymax = cymax;
+  if (cudaMemcpyAsync(fp->d_ff, &h, sizeof(FastField), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return 1;
+  // N >= 8 (two stages of 4 frames): the producer runs at most S stages (at
+  // most 48 frames) ahead of the slowest consumer, so fewer than 8 items are
+  // live and the 8 per-item slots never collide.  Bilinear reads one more
+  // column: lane 31 + ocol + 1 must stay in the box.
   const int ocol_max = fd.storage == ST_F32
                            ? Store<float>::kBoxW - kTX - (fp->bl ? 1 : 0)
                            : Store<__half>::kOColMax;
-  *fits = fp->h_maxes[0] <= ocol_max && fp->h_maxes[1] < kPatterns && fd.N <= kParamBytes &&
-          fd.N >= 8;
+  *fits = fp->h_maxes[0] <= ocol_max && fp->h_maxes[1] < kPatterns && fd.N >= 8;
+  return 1;
+}
+
+int launch_stack_fast_multi(const FieldDev* fds, FastPlan* const* fps, int n, float* dump_S,
+                            int32_t* dump_C, Pending* pend, int64_t pend_cap, Counters* ctr,
+                            cudaStream_t s) {
+  if (n < 1 || n > kMaxFields) return -1;
+  FastPlan* fp0 = fps[0];  // the variant of the launch
+  int nvar = 0;
+  const Variant* vars = variants_for(fds[0].storage, fp0->bl, &nvar);
+  const int vi = fp0->variant < nvar ? fp0->variant : 0;
+  const Variant& var = vars[vi];
+  const int ky = var.ky, boxh = ky + 3 + (fp0->bl ? 1 : 0);
+  const int boxw = fds[0].storage == ST_F32 ? Store<float>::kBoxW : Store<__half>::kBoxW;
+  for (int i = 0; i < n; ++i) {
+    FastPlan* fp = fps[i];
+    if (fds[i].storage != fds[0].storage || fp->bl != fp0->bl) return -1;
+    if (fp->encoded_for != fds[i].cube || fp->encoded_boxh != boxh) {
+      if (!encode_tile_map(&fp->tmap, fds[i], boxw, boxh)) return -1;
+      if (cudaMemcpyAsync(fp->d_map, &fp->tmap, sizeof(CUtensorMap), cudaMemcpyHostToDevice,
+                          s) != cudaSuccess)
+        return -1;
+      fp->encoded_for = fds[i].cube;
+      fp->encoded_boxh = boxh;
+    }
+  }
+  // fields longest first (the items of the most frames are taken first)
+  int order[kMaxFields];
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order, order + n, [&](int x, int y) { return fds[x].N > fds[y].N; });
+  thread_local static FastArgs a;
+  std::memset(&a, 0, sizeof a);
+  int64_t total = 0;
+  for (int i = 0; i < n; ++i) {
+    a.ff[i] = fps[order[i]]->d_ff;
+    a.maps[i] = fps[order[i]]->d_map;
+    total += items_of(fps[order[i]]->h_ff, ky);
+  }
+  a.n_fields = n;
+  a.n_items = fp0->item_limit > 0 && total > fp0->item_limit ? fp0->item_limit : total;
+  a.work = &ctr->work_next;
+  a.pend = pend;
+  a.cap = pend_cap;
+  a.ctr = ctr;
+  a.dump_S = dump_S;
+  a.dump_C = dump_C;
+  const int esz = fds[0].storage == ST_F32 ? 4 : 2;
+  const int stage_bytes = ((boxh * boxw * esz) + 127) & ~127;
+  void (*fn)(FastArgs) = dump_S ? var.dump_fn : var.fn;
+  const size_t smem = (size_t)var.stages * stage_bytes + 128;
+  static bool attr_set[2][3][2 * kNumVariants] = {};
+  const int attr_i = 2 * vi + (dump_S ? 1 : 0);
+  if (!attr_set[fp0->bl][fds[0].storage][attr_i]) {
+    cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set[fp0->bl][fds[0].storage][attr_i] = true;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaMemsetAsync(&ctr->work_next, 0, sizeof(ctr->work_next), s) != cudaSuccess) return -1;
+  const int per_sm = ky <= 16 ? 2 : 1;  // persistent CTAs per SM
+  const int64_t grid = a.n_items < (int64_t)sms * per_sm ? a.n_items : (int64_t)sms * per_sm;
+  if (grid < 1) return 0;
+  void* args[1] = {&a};
+  if (cudaLaunchKernel((const void*)fn, dim3((unsigned)grid), dim3(var.threads), args, smem, s) !=
+      cudaSuccess)
+    return -1;
   return 1;
 }
 
 int launch_stack_fast(const FieldDev& fd, const FastPlan* cfp, int k0, int nk,
                       const int32_t* dump_k, float* dump_S, int32_t* dump_C, Pending* pend,
                       int64_t pend_cap, Counters* ctr, cudaStream_t s) {
-  FastPlan* fp = const_cast<FastPlan*>(cfp);
   if (k0 != 0 || nk != fd.nvx * fd.nvy || dump_k) return -1;  // whole grid only
-  int nvar = 0;
-  const Variant* vars = variants_for(fd.storage, fp->bl, &nvar);
-  const Variant& var = vars[fp->variant < nvar ? fp->variant : 0];
-  const int ky = var.ky, boxh = ky + 3 + (fp->bl ? 1 : 0);
-  const int esz = fd.storage == ST_F32 ? 4 : 2;
-  const int boxw = fd.storage == ST_F32 ? Store<float>::kBoxW : Store<__half>::kBoxW;
-  const CUtensorMapDataType dtype = fd.storage == ST_F32    ? Store<float>::kTma
-                                    : fd.storage == ST_F16 ? Store<__half>::kTma
-                                                           : Store<__nv_bfloat16>::kTma;
-  if (fp->encoded_for != fd.cube || fp->encoded_boxh != boxh) {
-    cuuint64_t dims[3] = {(cuuint64_t)fd.W, (cuuint64_t)fd.H, (cuuint64_t)fd.N};
-    cuuint64_t strides[2] = {(cuuint64_t)fd.W * esz, (cuuint64_t)fd.W * fd.H * esz};
-    cuuint32_t box[3] = {(cuuint32_t)boxw, (cuuint32_t)boxh, 1};
-    cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = encode_fn()(&fp->tmap, dtype, 3,
-                             const_cast<void*>(fd.cube), dims, strides, box, estr,
-                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return -1;
-    fp->encoded_for = fd.cube;
-    fp->encoded_boxh = boxh;
-  }
-  thread_local static FastArgs a;  // large parameter-space block, filled per launch
-  std::memset(&a, 0, sizeof a);
-  a.W = fd.W;
-  a.H = fd.H;
-  a.N = fd.N;
-  a.nvx = fd.nvx;
-  a.nvy = fd.nvy;
-  a.nA = fp->nA;
-  a.nB = fp->nB;
-  int stage_bytes = ((boxh * boxw * esz) + 127) & ~127;
-  a.stage_floats = stage_bytes / esz;
-  a.ty_rows = ky;
-  a.tiles_x = (fd.W + kTX - 1) / kTX;
-  a.tiles_y = (fd.H + ky - 1) / ky;
-  a.super_x = (a.tiles_x + kSuper - 1) / kSuper;
-  a.super_y = (a.tiles_y + kSuper - 1) / kSuper;
-  a.nmin = fd.nmin;
-  a.field = fd.field;
-  a.xt = fp->xt;
-  a.yt = fp->yt;
-  a.xmin = fp->ranges;
-  a.xmax = fp->ranges + fp->nA;
-  a.ymin = fp->ranges + 2 * fp->nA;
-  a.ymax = fp->ranges + 2 * fp->nA + fp->nB;
-  a.sx = fd.sx;
-  a.sy = fd.sy;
-  a.fx = fd.fx;
-  a.fy = fd.fy;
-  a.fxt = reinterpret_cast<const float4*>(fp->fxt);
-  a.fyt = reinterpret_cast<const float4*>(fp->fyt);
-  a.thr = fd.thr;
-  a.cov_len = fp->cov_len;
-  a.covx = fp->cov;
-  a.covy = fp->cov + (int64_t)fd.nvx * fp->cov_len;
-  a.cov_xmin = a.covy + (int64_t)fd.nvy * fp->cov_len;
-  a.cov_xmax = a.cov_xmin + fd.nvx;
-  a.cov_ymin = a.cov_xmax + fd.nvx;
-  a.cov_ymax = a.cov_ymin + fd.nvy;
-  a.pend = pend;
-  a.cap = pend_cap;
-  a.ctr = ctr;
-  a.dump_S = dump_S;
-  a.dump_C = dump_C;
-  void (*fn)(CUtensorMap, FastArgs) = dump_S ? var.dump_fn : var.fn;
-  size_t smem = (size_t)var.stages * stage_bytes + 128;
-  static bool attr_set[2][3][2 * kNumVariants] = {};
-  const int attr_i = 2 * (fp->variant < nvar ? fp->variant : 0) + (dump_S ? 1 : 0);
-  if (!attr_set[fp->bl][fd.storage][attr_i]) {
-    cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set[fp->bl][fd.storage][attr_i] = true;
-  }
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int F_var = var.stages_f;  // frames per stage of the variant
-  const int Np = ((fd.N + F_var - 1) / F_var) * F_var;  // item frames padded to whole stages
-  const int G = kParamBytes / Np < fp->nB ? kParamBytes / Np : fp->nB;
-  if (G < 1) return -1;
-  int launches = 0;
-  for (int B0 = 0; B0 < fp->nB; B0 += G) {
-    if (fp->item_limit > 0 && B0 > 0) break;  // autotuning samples the first launch only
-    a.B0 = B0;
-    a.G = fp->nB - B0 < G ? fp->nB - B0 : G;
-    for (int g = 0; g < a.G; ++g)
-      for (int i = 0; i < Np; ++i)
-        a.pat[g * Np + i] =
-            i < fd.N ? fp->h_pat[(size_t)i * fp->nB + B0 + g] : (unsigned char)kPatterns;
-    a.n_items = (int64_t)a.super_x * a.super_y * kSuper * kSuper * a.nA * a.G;
-    if (fp->item_limit > 0 && a.n_items > fp->item_limit) a.n_items = fp->item_limit;
-    const int per_sm = ky <= 16 ? 2 : 1;  // persistent CTAs per SM
-    const int64_t grid = a.n_items < (int64_t)sms * per_sm ? a.n_items : (int64_t)sms * per_sm;
-    void* args[2] = {&fp->tmap, &a};
-    if (cudaLaunchKernel((const void*)fn, dim3((unsigned)grid), dim3(var.threads), args, smem, s) !=
-        cudaSuccess)
-      return -1;
-    ++launches;
-  }
-  return launches;
+  FastPlan* fp = const_cast<FastPlan*>(cfp);
+  return launch_stack_fast_multi(&fd, &fp, 1, dump_S, dump_C, pend, pend_cap, ctr, s);
 }
 
 }  // namespace st

@@ -279,44 +279,71 @@ st_status device_search(st_plan_t* p, const float* const* d_frames, const double
   }
   CK(cudaMemcpyAsync(p->d_fds, fds.data(), sizeof(FieldDev) * nf, cudaMemcpyHostToDevice, p->s));
   CK(cudaMemsetAsync(p->d_ctr, 0, sizeof(Counters), p->s));
+  // fields that fit the register-window kernel run in one persistent launch;
+  // its variant is tuned (or looked up) on the field with the most work
   std::vector<char> use_fast(nf, 0);
-  bool tuned_now = false;
+  std::vector<FieldDev> fast_fds;
+  std::vector<FastPlan*> fast_fps;
+  int tune_fi = -1;
   for (int fi = 0; fi < nf; ++fi) {
     bool fits = false;
     FieldPlan& fp = p->F[fi];
     if (fp.fast) {
       L += fast_prepare(fds[fi], fp.fast, p->s, &fits);
       CK(cudaGetLastError());
-      if (fits && p->o.tile == -1 && !fp.tuned) {
-        const std::string key = tune_key(fp.f, fds[fi].storage, p->o.mode, p->sms);
-        int v = tune_lookup(p->tune_cache, key);
-        if (v >= 0 && v < fast_num_variants_for(fp.fast, fds[fi].storage)) {
-          fast_set_variant(fp.fast, v);
-        } else {
-          L += fast_autotune(fds[fi], fp.fast, 8ll * p->sms, p->d_pend, p->pend_cap, p->d_ctr,
-                             p->s);
-          tune_store(p->tune_cache, key, fast_get_variant(fp.fast));
-          tuned_now = true;
-        }
-        fp.tuned = true;
-      }
     }
     use_fast[fi] = fits;
+    if (fits) {
+      fast_fds.push_back(fds[fi]);
+      fast_fps.push_back(fp.fast);
+      const double work = (double)fp.P() * fp.f.n_frames * fp.nk();
+      if (tune_fi < 0 || work > (double)p->F[tune_fi].P() * p->F[tune_fi].f.n_frames *
+                                    p->F[tune_fi].nk())
+        tune_fi = fi;
+    }
+  }
+  bool tuned_now = false;
+  if (tune_fi >= 0 && p->o.tile == -1) {
+    FieldPlan& tp = p->F[tune_fi];
+    if (!tp.tuned) {
+      const std::string key = tune_key(tp.f, fds[tune_fi].storage, p->o.mode, p->sms);
+      int v = tune_lookup(p->tune_cache, key);
+      if (v >= 0 && v < fast_num_variants_for(tp.fast, fds[tune_fi].storage)) {
+        fast_set_variant(tp.fast, v);
+      } else {
+        L += fast_autotune(fds[tune_fi], tp.fast, 8ll * p->sms, p->d_pend, p->pend_cap,
+                           p->d_ctr, p->s);
+        tune_store(p->tune_cache, key, fast_get_variant(tp.fast));
+        tuned_now = true;
+      }
+      tp.tuned = true;
+    }
+    for (FastPlan* f : fast_fps) fast_set_variant(f, fast_get_variant(tp.fast));
   }
   if (tuned_now) CK(cudaMemsetAsync(p->d_ctr, 0, sizeof(Counters), p->s));
   CK(cudaEventRecord(p->e0, p->s));
   int64_t stack_launches = 0;
+  if (!fast_fds.empty()) {
+    // the field with the most work first: its variant is the launch's
+    for (size_t i = 0; i < fast_fds.size(); ++i)
+      if (fast_fds[i].field == tune_fi) {
+        std::swap(fast_fds[0], fast_fds[i]);
+        std::swap(fast_fps[0], fast_fps[i]);
+      }
+    int n = launch_stack_fast_multi(fast_fds.data(), fast_fps.data(), (int)fast_fds.size(),
+                                    nullptr, nullptr, p->d_pend, p->pend_cap, p->d_ctr, p->s);
+    if (n < 0)  // not launchable: every field takes the direct-gather kernel
+      for (int fi = 0; fi < nf; ++fi) use_fast[fi] = 0;
+    else
+      stack_launches += n;
+  }
   for (int fi = 0; fi < nf; ++fi) {
     FieldPlan& fp = p->F[fi];
-    int n = -1;
-    if (use_fast[fi])
-      n = launch_stack_fast(fds[fi], fp.fast, 0, (int)fp.nk(), nullptr, nullptr, nullptr,
-                            p->d_pend, p->pend_cap, p->d_ctr, p->s);
-    fp.last_variant = n >= 0 ? 1 : 0;
-    if (n < 0)
-      n = launch_stack_generic(fds[fi], p->o.mode, 0, (int)fp.nk(), nullptr, nullptr, nullptr,
-                               p->d_pend, p->pend_cap, p->d_ctr, p->s);
-    stack_launches += n;
+    fp.last_variant = use_fast[fi] ? 1 : 0;
+    if (!use_fast[fi])
+      stack_launches += launch_stack_generic(fds[fi], p->o.mode, 0, (int)fp.nk(), nullptr,
+                                             nullptr, nullptr, p->d_pend, p->pend_cap, p->d_ctr,
+                                             p->s);
   }
   CK(cudaEventRecord(p->e1, p->s));
   L += stack_launches;

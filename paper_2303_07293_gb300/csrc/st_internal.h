@@ -95,6 +95,11 @@ void fast_plan_free(FastPlan* fp);
 int launch_stack_fast(const FieldDev& fd, const FastPlan* fp, int k0, int nk,
                       const int32_t* dump_k, float* dump_S, int32_t* dump_C, Pending* pend,
                       int64_t pend_cap, Counters* ctr, cudaStream_t s);
+// One persistent launch over n prepared, fitting fields (same storage and
+// sampling; the variant of fps[0]), items taken longest field first.
+int launch_stack_fast_multi(const FieldDev* fds, FastPlan* const* fps, int n, float* dump_S,
+                            int32_t* dump_C, Pending* pend, int64_t pend_cap, Counters* ctr,
+                            cudaStream_t s);
 
 // Local-maximum test of the pending points -> candidate list (unsorted) and keys.
 int launch_resolve(const FieldDev* fds_dev, int n_fields, int mode, const Pending* pend,

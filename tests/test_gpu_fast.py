@@ -185,3 +185,42 @@ def test_multi_field_plan_equals_single_field_plans(st):
         assert mine[["x", "y", "k", "n_cov"]].tolist() == c[["x", "y", "k", "n_cov"]].tolist()
         assert np.array_equal(mine["stack"], c["stack"])
     assert np.all(np.diff(allc["field"]) >= 0)   # sorted by field first
+
+
+@pytest.mark.parametrize("mode", ["nearest", "bilinear"])
+def test_batched_fields_one_persistent_launch(st, mode):
+    # uneven frame counts, sizes and grids in one plan: every field that fits
+    # the register-window kernel runs in ONE persistent launch (items taken
+    # longest field first); a field whose motion does not fit (wide span)
+    # takes the direct-gather kernel.  Each field's candidates equal its
+    # single-field plan's and, for nearest shifts, the oracle's.
+    specs = [dict(seed=31, W=96, H=64, N=20, nvx=9, nvy=8),
+             dict(seed=32, W=160, H=40, N=57, nvx=19, nvy=6, dv=0.12),
+             dict(seed=33, W=64, H=72, N=9, nvx=8, nvy=13),
+             dict(seed=34, W=128, H=33, N=41, nvx=5, nvy=17, dv=0.2, ref=-1),
+             dict(seed=35, W=80, H=48, N=16, nvx=9, nvy=9, dv=2.0)]   # does not fit
+    fields = [field(**sp) for sp in specs]
+    singles = []
+    for fr, t, f in fields:
+        with st.Plan(f, mode=mode) as p:
+            singles.append(p.candidates(dev(fr), t))
+    with st.Plan([f for _, _, f in fields], mode=mode) as p:
+        out, n, status = p.search([dev(fr) for fr, _, _ in fields], [t for _, t, _ in fields],
+                                  capacity=1 << 18)
+        allc = p.to_numpy(out, n)
+        used = [p.last_stack_variant(i) for i in range(len(fields))]
+        _, stack_launches = p.last_stack_kernel_time()
+    assert status == st.ST_OK
+    assert used == [1, 1, 1, 1, 0]
+    assert stack_launches == 2      # one persistent launch + the direct-gather field
+    for i, c in enumerate(singles):
+        mine = allc[allc["field"] == i]
+        assert mine.tobytes() == c.tobytes() or (
+            mine[["x", "y", "k", "n_cov"]].tolist() == c[["x", "y", "k", "n_cov"]].tolist() and
+            np.array_equal(mine["stack"], c["stack"])), i
+        if mode == "nearest":
+            fr, t, f = fields[i]
+            ref = oracle.search(fr, t, f, prec="fp32")
+            assert mine[["x", "y", "k", "n_cov"]].tolist() == \
+                ref[["x", "y", "k", "n_cov"]].tolist(), i
+    assert np.all(np.diff(allc["field"]) >= 0)
