@@ -257,6 +257,12 @@ st_status st_last_stack_kernel_time(const st_plan_t* plan, double* ms, int64_t* 
  * 1 = register-window kernel, 0 = direct-gather kernel, -1 = no search yet. */
 int32_t st_last_stack_variant(const st_plan_t* plan, int32_t field);
 
+/* 1 if the device part of the last search (normalisation, stack, local
+ * maxima) ran as a CUDA graph (use_graph: captured on the first search with
+ * given frame pointers and timestamps, replayed while they stay the same),
+ * 0 otherwise. */
+int32_t st_last_graph_replayed(const st_plan_t* plan);
+
 /* FP32 add-rate microbenchmark (the roof of the nearest-shift stack): one
  * block of 1024 threads per SM, 16 independent add chains per thread, iters
  * iterations.  variant 0: scalar add.rn.f32; 1: paired add.rn.f32x2;

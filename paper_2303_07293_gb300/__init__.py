@@ -78,6 +78,8 @@ def lib():
         L.st_last_stack_kernel_time.argtypes = [P, P, P]
         L.st_last_stack_variant.argtypes = [P, C.c_int32]
         L.st_last_stack_variant.restype = C.c_int32
+        L.st_last_graph_replayed.argtypes = [P]
+        L.st_last_graph_replayed.restype = C.c_int32
         L.st_probe_add_rate.argtypes = [C.c_int32, C.c_int32, P, P]
         _lib = L
     return _lib
@@ -272,6 +274,10 @@ class Plan:
         """1 if field used the register-window kernel in the last search, 0 if
         the direct-gather kernel, -1 before any search."""
         return lib().st_last_stack_variant(self._h, field)
+
+    def last_graph_replayed(self):
+        """True if the last search's device part ran as a CUDA graph."""
+        return bool(lib().st_last_graph_replayed(self._h))
 
     def last_launch_count(self):
         return lib().st_last_launch_count(self._h)

@@ -1016,29 +1016,60 @@ int fast_prepare(const FieldDev& fd, FastPlan* fp, cudaStream_t s, bool* fits) {
   return 1;
 }
 
-int launch_stack_fast_multi(const FieldDev* fds, FastPlan* const* fps, int n, float* dump_S,
-                            int32_t* dump_C, Pending* pend, int64_t pend_cap, Counters* ctr,
-                            cudaStream_t s) {
-  if (n < 1 || n > kMaxFields) return -1;
-  FastPlan* fp0 = fps[0];  // the variant of the launch
+// The launch's variant (that of fps[0]) and, for every field, its cube's
+// tiled map for that variant's box, encoded and copied to the device when the
+// cube or the box changed (pageable source: staged before the call returns).
+static const Variant* stage_maps(const FieldDev* fds, FastPlan* const* fps, int n,
+                                 cudaStream_t s, bool* restaged, int* vi_out) {
+  if (n < 1 || n > kMaxFields) return nullptr;
+  FastPlan* fp0 = fps[0];
   int nvar = 0;
   const Variant* vars = variants_for(fds[0].storage, fp0->bl, &nvar);
   const int vi = fp0->variant < nvar ? fp0->variant : 0;
   const Variant& var = vars[vi];
-  const int ky = var.ky, boxh = ky + 3 + (fp0->bl ? 1 : 0);
+  const int boxh = var.ky + 3 + (fp0->bl ? 1 : 0);
   const int boxw = fds[0].storage == ST_F32 ? Store<float>::kBoxW : Store<__half>::kBoxW;
   for (int i = 0; i < n; ++i) {
     FastPlan* fp = fps[i];
-    if (fds[i].storage != fds[0].storage || fp->bl != fp0->bl) return -1;
+    if (fds[i].storage != fds[0].storage || fp->bl != fp0->bl) return nullptr;
     if (fp->encoded_for != fds[i].cube || fp->encoded_boxh != boxh) {
-      if (!encode_tile_map(&fp->tmap, fds[i], boxw, boxh)) return -1;
+      if (!encode_tile_map(&fp->tmap, fds[i], boxw, boxh)) return nullptr;
       if (cudaMemcpyAsync(fp->d_map, &fp->tmap, sizeof(CUtensorMap), cudaMemcpyHostToDevice,
                           s) != cudaSuccess)
-        return -1;
+        return nullptr;
       fp->encoded_for = fds[i].cube;
       fp->encoded_boxh = boxh;
+      if (restaged) *restaged = true;
     }
   }
+  // kernel attributes are set once per compiled kernel
+  static bool attr_set[2][3][2 * kNumVariants] = {};
+  for (int d = 0; d < 2; ++d)
+    if (!attr_set[fp0->bl][fds[0].storage][2 * vi + d]) {
+      cudaFuncSetAttribute((const void*)(d ? var.dump_fn : var.fn),
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr_set[fp0->bl][fds[0].storage][2 * vi + d] = true;
+    }
+  *vi_out = vi;
+  return &var;
+}
+
+bool fast_stage(const FieldDev* fds, FastPlan* const* fps, int n, cudaStream_t s,
+                bool* restaged) {
+  int vi = 0;
+  return stage_maps(fds, fps, n, s, restaged, &vi) != nullptr;
+}
+
+int launch_stack_fast_multi(const FieldDev* fds, FastPlan* const* fps, int n, float* dump_S,
+                            int32_t* dump_C, Pending* pend, int64_t pend_cap, Counters* ctr,
+                            cudaStream_t s) {
+  FastPlan* fp0 = fps[0];  // the variant of the launch
+  int vi = 0;
+  const Variant* vp = stage_maps(fds, fps, n, s, nullptr, &vi);
+  if (!vp) return -1;
+  const Variant& var = *vp;
+  const int ky = var.ky, boxh = ky + 3 + (fp0->bl ? 1 : 0);
+  const int boxw = fds[0].storage == ST_F32 ? Store<float>::kBoxW : Store<__half>::kBoxW;
   // fields longest first (the items of the most frames are taken first)
   int order[kMaxFields];
   for (int i = 0; i < n; ++i) order[i] = i;
@@ -1063,12 +1094,6 @@ int launch_stack_fast_multi(const FieldDev* fds, FastPlan* const* fps, int n, fl
   const int stage_bytes = ((boxh * boxw * esz) + 127) & ~127;
   void (*fn)(FastArgs) = dump_S ? var.dump_fn : var.fn;
   const size_t smem = (size_t)var.stages * stage_bytes + 128;
-  static bool attr_set[2][3][2 * kNumVariants] = {};
-  const int attr_i = 2 * vi + (dump_S ? 1 : 0);
-  if (!attr_set[fp0->bl][fds[0].storage][attr_i]) {
-    cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set[fp0->bl][fds[0].storage][attr_i] = true;
-  }
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -74,6 +74,10 @@ struct FieldPlan {
   int last_variant = -1;
   bool tuned = false;
   const float* last_frames = nullptr;
+  std::vector<double> h_t;     // timestamps the shift tables were built for
+  bool tables_valid = false;   // shift tables match h_t
+  bool fast_ready = false;     // register-window tables built for the current shift tables
+  bool fast_fits = false;      // and the field's motion fits the kernel
   int64_t P() const { return (int64_t)f.width * f.height; }
   int64_t nk() const { return (int64_t)f.nvx * f.nvy; }
 };
@@ -107,6 +111,17 @@ struct st_plan_s {
   int64_t stack_launches = 0;
   int64_t launches = 0;
   bool has_search = false;
+  // CUDA graph of the device part of a search (normalise, stack, resolve),
+  // valid for the frame pointers and table generation it was captured with
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t cap_s = nullptr;  // capture stream (the plan's stream may be the legacy one)
+  std::vector<const float*> graph_frames;
+  uint64_t graph_gen = 0;
+  uint64_t gen = 1;             // bumped when tables, variants or maps change
+  int64_t graph_stack_launches = 0;
+  int64_t graph_launches = 0;
+  bool graph_broken = false;    // capture failed once: run directly
+  bool last_replayed = false;
 };
 
 namespace {
@@ -126,6 +141,8 @@ void free_plan(st_plan_t* p) {
     cudaFree(fp.d_frames_copy);
     if (fp.fast) fast_plan_free(fp.fast);
   }
+  if (p->graph) cudaGraphExecDestroy(p->graph);
+  if (p->cap_s) cudaStreamDestroy(p->cap_s);
   cudaFree(p->d_pend);
   cudaFree(p->d_ctr);
   cudaFree(p->d_maps);
@@ -223,21 +240,46 @@ void tune_store(const std::string& path, const std::string& key, int variant) {
   }
 }
 
-// Tables + optional normalisation for field fi with the given frames/times.
-st_status prepare_field(st_plan_t* p, int fi, const float* d_frames, const double* h_times,
-                        int64_t* launches) {
+// Shift tables of field fi for the given timestamps; rebuilt only when the
+// timestamps differ from those of the current tables.
+st_status prepare_tables(st_plan_t* p, int fi, const double* h_times, int64_t* launches,
+                         bool* changed) {
   FieldPlan& fp = p->F[fi];
   const st_field& f = fp.f;
   st_status st = check_times(h_times, f.n_frames, f, fi);
   if (st != ST_OK) return st;
+  *changed = false;
+  if (fp.tables_valid && fp.h_t.size() == (size_t)f.n_frames &&
+      std::memcmp(fp.h_t.data(), h_times, sizeof(double) * f.n_frames) == 0)
+    return ST_OK;
   CK(cudaMemcpyAsync(fp.d_t, h_times, sizeof(double) * f.n_frames, cudaMemcpyHostToDevice, p->s));
   *launches += launch_shift_tables(fp.d_t, f.n_frames, f.t_ref, f.vx0, f.dvx, f.nvx, f.vy0, f.dvy,
                                    f.nvy, p->o.mode, fp.d_sx, fp.d_sy, fp.d_fx, fp.d_fy, p->s);
-  if (fp.d_cube) {
-    *launches += launch_normalize(d_frames, f.n_frames, fp.P(), p->o.normalize, p->o.cr_clip,
-                                  p->o.storage, fp.d_cube, nullptr, nullptr, p->d_sky, p->s);
-  }
+  CK(cudaGetLastError());
+  fp.h_t.assign(h_times, h_times + f.n_frames);
+  fp.tables_valid = true;
+  fp.fast_ready = false;
+  ++p->gen;
+  *changed = true;
+  return ST_OK;
+}
+
+// Optional normalisation / storage conversion of field fi into the plan's cube.
+int64_t normalize_field(st_plan_t* p, int fi, const float* d_frames) {
+  FieldPlan& fp = p->F[fi];
   fp.last_frames = d_frames;
+  if (!fp.d_cube) return 0;
+  return launch_normalize(d_frames, fp.f.n_frames, fp.P(), p->o.normalize, p->o.cr_clip,
+                          p->o.storage, fp.d_cube, nullptr, nullptr, p->d_sky, p->s);
+}
+
+// Tables + optional normalisation for field fi with the given frames/times.
+st_status prepare_field(st_plan_t* p, int fi, const float* d_frames, const double* h_times,
+                        int64_t* launches) {
+  bool changed = false;
+  st_status st = prepare_tables(p, fi, h_times, launches, &changed);
+  if (st != ST_OK) return st;
+  *launches += normalize_field(p, fi, d_frames);
   CK(cudaGetLastError());
   return ST_OK;
 }
@@ -270,15 +312,17 @@ st_status device_search(st_plan_t* p, const float* const* d_frames, const double
   int nf = (int)p->F.size();
   for (int fi = 0; fi < nf; ++fi)
     if (!d_frames[fi]) return fail(ST_ERR_INVALID, "field %d: frames are NULL", fi);
+  // ---- host-side preparation: tables (when the timestamps change), the
+  // register-window tables and variant, the tensor maps
   int64_t L = 0;
   std::vector<FieldDev> fds(nf);
   for (int fi = 0; fi < nf; ++fi) {
-    st_status st = prepare_field(p, fi, d_frames[fi], h_times[fi], &L);
+    bool changed = false;
+    st_status st = prepare_tables(p, fi, h_times[fi], &L, &changed);
     if (st != ST_OK) return st;
     fds[fi] = field_dev(p->F[fi], d_frames[fi], fi, p->o.storage);
   }
   CK(cudaMemcpyAsync(p->d_fds, fds.data(), sizeof(FieldDev) * nf, cudaMemcpyHostToDevice, p->s));
-  CK(cudaMemsetAsync(p->d_ctr, 0, sizeof(Counters), p->s));
   // fields that fit the register-window kernel run in one persistent launch;
   // its variant is tuned (or looked up) on the field with the most work
   std::vector<char> use_fast(nf, 0);
@@ -286,14 +330,16 @@ st_status device_search(st_plan_t* p, const float* const* d_frames, const double
   std::vector<FastPlan*> fast_fps;
   int tune_fi = -1;
   for (int fi = 0; fi < nf; ++fi) {
-    bool fits = false;
     FieldPlan& fp = p->F[fi];
-    if (fp.fast) {
+    if (fp.fast && !fp.fast_ready) {
+      bool fits = false;
       L += fast_prepare(fds[fi], fp.fast, p->s, &fits);
       CK(cudaGetLastError());
+      fp.fast_fits = fits;
+      fp.fast_ready = true;
     }
-    use_fast[fi] = fits;
-    if (fits) {
+    use_fast[fi] = fp.fast && fp.fast_fits;
+    if (use_fast[fi]) {
       fast_fds.push_back(fds[fi]);
       fast_fps.push_back(fp.fast);
       const double work = (double)fp.P() * fp.f.n_frames * fp.nk();
@@ -302,7 +348,6 @@ st_status device_search(st_plan_t* p, const float* const* d_frames, const double
         tune_fi = fi;
     }
   }
-  bool tuned_now = false;
   if (tune_fi >= 0 && p->o.tile == -1) {
     FieldPlan& tp = p->F[tune_fi];
     if (!tp.tuned) {
@@ -311,18 +356,17 @@ st_status device_search(st_plan_t* p, const float* const* d_frames, const double
       if (v >= 0 && v < fast_num_variants_for(tp.fast, fds[tune_fi].storage)) {
         fast_set_variant(tp.fast, v);
       } else {
+        // the variants are timed on the field's frames as the search reads them
+        L += normalize_field(p, tune_fi, d_frames[tune_fi]);
         L += fast_autotune(fds[tune_fi], tp.fast, 8ll * p->sms, p->d_pend, p->pend_cap,
                            p->d_ctr, p->s);
         tune_store(p->tune_cache, key, fast_get_variant(tp.fast));
-        tuned_now = true;
       }
       tp.tuned = true;
+      ++p->gen;
     }
     for (FastPlan* f : fast_fps) fast_set_variant(f, fast_get_variant(tp.fast));
   }
-  if (tuned_now) CK(cudaMemsetAsync(p->d_ctr, 0, sizeof(Counters), p->s));
-  CK(cudaEventRecord(p->e0, p->s));
-  int64_t stack_launches = 0;
   if (!fast_fds.empty()) {
     // the field with the most work first: its variant is the launch's
     for (size_t i = 0; i < fast_fds.size(); ++i)
@@ -330,27 +374,104 @@ st_status device_search(st_plan_t* p, const float* const* d_frames, const double
         std::swap(fast_fds[0], fast_fds[i]);
         std::swap(fast_fps[0], fast_fps[i]);
       }
-    int n = launch_stack_fast_multi(fast_fds.data(), fast_fps.data(), (int)fast_fds.size(),
-                                    nullptr, nullptr, p->d_pend, p->pend_cap, p->d_ctr, p->s);
-    if (n < 0)  // not launchable: every field takes the direct-gather kernel
-      for (int fi = 0; fi < nf; ++fi) use_fast[fi] = 0;
-    else
-      stack_launches += n;
+    bool restaged = false;
+    if (!fast_stage(fast_fds.data(), fast_fps.data(), (int)fast_fds.size(), p->s, &restaged)) {
+      for (int fi = 0; fi < nf; ++fi) use_fast[fi] = 0;  // every field: direct gather
+      fast_fds.clear();
+    }
+    if (restaged) ++p->gen;
   }
-  for (int fi = 0; fi < nf; ++fi) {
-    FieldPlan& fp = p->F[fi];
-    fp.last_variant = use_fast[fi] ? 1 : 0;
-    if (!use_fast[fi])
-      stack_launches += launch_stack_generic(fds[fi], p->o.mode, 0, (int)fp.nk(), nullptr,
-                                             nullptr, nullptr, p->d_pend, p->pend_cap, p->d_ctr,
-                                             p->s);
+  for (int fi = 0; fi < nf; ++fi) p->F[fi].last_variant = use_fast[fi] ? 1 : 0;
+
+  // ---- the device part of the search: normalise, stack, resolve, counters.
+  // Errors are collected, not returned, so that a capture always ends.
+  bool capturing = false;
+  auto record = [&](cudaEvent_t ev) {
+    // inside a capture the timing events become event-record nodes of the graph
+    return capturing ? cudaEventRecordWithFlags(ev, p->s, cudaEventRecordExternal)
+                     : cudaEventRecord(ev, p->s);
+  };
+  auto issue = [&](int64_t* stack_launches, int64_t* launches) -> cudaError_t {
+    cudaError_t e = cudaMemsetAsync(p->d_ctr, 0, sizeof(Counters), p->s);
+    for (int fi = 0; fi < nf; ++fi) *launches += normalize_field(p, fi, d_frames[fi]);
+    if (e == cudaSuccess) e = record(p->e0);
+    if (!fast_fds.empty()) {
+      int n = launch_stack_fast_multi(fast_fds.data(), fast_fps.data(), (int)fast_fds.size(),
+                                      nullptr, nullptr, p->d_pend, p->pend_cap, p->d_ctr, p->s);
+      if (n < 0 && e == cudaSuccess) e = cudaErrorLaunchFailure;
+      *stack_launches += n > 0 ? n : 0;
+    }
+    for (int fi = 0; fi < nf; ++fi)
+      if (!use_fast[fi])
+        *stack_launches += launch_stack_generic(fds[fi], p->o.mode, 0, (int)p->F[fi].nk(),
+                                                nullptr, nullptr, nullptr, p->d_pend,
+                                                p->pend_cap, p->d_ctr, p->s);
+    if (e == cudaSuccess) e = record(p->e1);
+    *launches += launch_resolve(p->d_fds, nf, p->o.mode, p->d_pend, p->d_ctr, p->pend_cap,
+                                p->d_cand, p->d_keys, p->d_idx, p->pend_cap, p->d_ctr, p->s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(p->h_ctr, p->d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, p->s);
+    return e;
+  };
+  int64_t stack_launches = 0, dev_launches = 0;
+  p->last_replayed = false;
+  bool done = false;
+  if (p->o.use_graph && !p->graph_broken) {
+    std::vector<const float*> key(d_frames, d_frames + nf);
+    if (!(p->graph && p->graph_gen == p->gen && p->graph_frames == key)) {
+      // capture the device part once for these frames and tables
+      if (p->graph) {
+        cudaGraphExecDestroy(p->graph);
+        p->graph = nullptr;
+      }
+      // captured on a plan-owned stream (the plan's own stream may be the
+      // legacy default stream, which cannot be captured), launched on the
+      // plan's stream
+      cudaGraph_t g = nullptr;
+      int64_t sl = 0, dl = 0;
+      cudaError_t e = cudaSuccess;
+      if (!p->cap_s) e = cudaStreamCreateWithFlags(&p->cap_s, cudaStreamNonBlocking);
+      const cudaStream_t user_s = p->s;
+      if (e == cudaSuccess) e = cudaStreamBeginCapture(p->cap_s, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        p->s = p->cap_s;
+        capturing = true;
+        cudaError_t e2 = issue(&sl, &dl);
+        capturing = false;
+        p->s = user_s;
+        e = cudaStreamEndCapture(p->cap_s, &g);
+        if (e == cudaSuccess) e = e2;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&p->graph, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        set_last_error((std::string("graph capture failed, running directly: ") +
+                        cudaGetErrorString(e)).c_str());
+        cudaGetLastError();  // clear a capture error; run directly from now on
+        if (p->graph) cudaGraphExecDestroy(p->graph);
+        p->graph = nullptr;
+        p->graph_broken = true;
+      } else {
+        p->graph_frames = key;
+        p->graph_gen = p->gen;
+        p->graph_stack_launches = sl;
+        p->graph_launches = dl;
+      }
+    }
+    if (p->graph) {
+      CK(cudaGraphLaunch(p->graph, p->s));
+      stack_launches = p->graph_stack_launches;
+      dev_launches = p->graph_launches;
+      p->last_replayed = true;
+      done = true;
+    }
   }
-  CK(cudaEventRecord(p->e1, p->s));
-  L += stack_launches;
-  L += launch_resolve(p->d_fds, nf, p->o.mode, p->d_pend, p->d_ctr, p->pend_cap, p->d_cand,
-                      p->d_keys, p->d_idx, p->pend_cap, p->d_ctr, p->s);
-  CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(p->h_ctr, p->d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, p->s));
+  if (!done) {
+    cudaError_t e = issue(&stack_launches, &dev_launches);
+    if (e != cudaSuccess) return fail(ST_ERR_CUDA, "search: %s", cudaGetErrorString(e));
+  }
+  L += stack_launches + dev_launches;
   CK(cudaStreamSynchronize(p->s));
   float ms = 0.0f;
   CK(cudaEventElapsedTime(&ms, p->e0, p->e1));
@@ -363,6 +484,11 @@ st_status device_search(st_plan_t* p, const float* const* d_frames, const double
     return fail(ST_ERR_OVERFLOW,
                 "%llu above-threshold points exceed pending_capacity %lld; raise it in st_opts",
                 (unsigned long long)c.n_pending, (long long)p->pend_cap);
+  }
+  if (c.error & ERR_TIMEOUT) {
+    *h_count = -1;
+    p->launches = L;
+    return fail(ST_ERR_TIMEOUT, "stack kernel: a pipeline wait gave up after 2 s");
   }
   int64_t n = (int64_t)c.n_cand;
   int64_t sn = pow2_at_least(std::max<int64_t>(n, 1));
@@ -580,6 +706,9 @@ st_status st_shift_tables(st_plan_t* p, int32_t field, const double* h_times, in
   const st_field& f = fp.f;
   st_status st = check_times(h_times, f.n_frames, f, field);
   if (st != ST_OK) return st;
+  // the field's tables now hold these timestamps' shifts: rebuild on the next search
+  fp.tables_valid = false;
+  ++p->gen;
   CK(cudaMemcpyAsync(fp.d_t, h_times, sizeof(double) * f.n_frames, cudaMemcpyHostToDevice, p->s));
   launch_shift_tables(fp.d_t, f.n_frames, f.t_ref, f.vx0, f.dvx, f.nvx, f.vy0, f.dvy, f.nvy,
                       p->o.mode, fp.d_sx, fp.d_sy, fp.d_fx, fp.d_fy, p->s);
@@ -655,6 +784,8 @@ st_status st_dump_stack(st_plan_t* p, int32_t field, const float* d_frames, cons
 }
 
 int64_t st_last_launch_count(const st_plan_t* p) { return p ? p->launches : 0; }
+
+int32_t st_last_graph_replayed(const st_plan_t* p) { return p && p->last_replayed ? 1 : 0; }
 
 int32_t st_last_stack_variant(const st_plan_t* p, int32_t field) {
   if (!p || field < 0 || field >= (int)p->F.size()) return -1;

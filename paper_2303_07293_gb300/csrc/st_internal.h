@@ -97,6 +97,10 @@ int launch_stack_fast(const FieldDev& fd, const FastPlan* fp, int k0, int nk,
                       int64_t pend_cap, Counters* ctr, cudaStream_t s);
 // One persistent launch over n prepared, fitting fields (same storage and
 // sampling; the variant of fps[0]), items taken longest field first.
+// Encodes and uploads the tensor maps a launch over these fields needs (so the
+// launch itself copies nothing); *restaged tells whether any map changed.
+bool fast_stage(const FieldDev* fds, FastPlan* const* fps, int n, cudaStream_t s,
+                bool* restaged);
 int launch_stack_fast_multi(const FieldDev* fds, FastPlan* const* fps, int n, float* dump_S,
                             int32_t* dump_C, Pending* pend, int64_t pend_cap, Counters* ctr,
                             cudaStream_t s);
