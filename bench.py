@@ -45,7 +45,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="speculoos", choices=list(WORKLOADS))
-    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--storage", default=None, choices=["f32", "f16", "bf16"],
+                    help="frame storage (default: f16 for the batched workload, else f32)")
+    ap.add_argument("--graph", type=int, default=None,
+                    help="capture the search in a CUDA graph (default: 1 for batched)")
     ap.add_argument("--mode", default="nearest", choices=["nearest", "bilinear"])
     ap.add_argument("--normalize", type=int, default=1)
     ap.add_argument("--cr-clip", type=float, default=10.0,
@@ -55,7 +58,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tile", type=int, default=-1,
                     help="-1 autotune (first warm-up step), 0 default, 1 direct-gather, 2.. variant")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.storage is None:
+        args.storage = "f16" if args.workload == "batched" else "f32"
+    if args.graph is None:
+        args.graph = 1 if args.workload == "batched" else 0
+    return args
 
 
 class Clocks:
@@ -149,14 +157,23 @@ def oracle_baseline(d, seconds, mode="nearest"):
                               f"full {W}x{H}x{N} field, {kind} oracle"), el
 
 
-def field_for(args, rank):
+BATCH = 24
+
+
+def field_for(args, rank, world):
+    """The rank's input: for the batched workload its share of the 24 fields
+    (longest-work-first assignment: total work fixed, strong scaling), else a
+    field of its own (weak scaling)."""
     import synth
     w = WORKLOADS[args.workload]["name"]
-    seed = synth.BASE_SEED + {"tiny": 1, "mid": 2, "speculoos": 3, "batched": 4,
-                              "refine": 5}[w] + 100000 * rank
+    base = synth.BASE_SEED + {"tiny": 1, "mid": 2, "speculoos": 3, "batched": 4, "refine": 5}[w]
     if w == "batched":
-        return [synth.make_field(w, seed=seed, index=j) for j in range(24)]
-    return synth.make_field(w, seed=seed)
+        from paper_2303_07293_gb300 import shard
+        specs = [synth.batched_field(base, j) for j in range(BATCH)]
+        mine = shard.assign_fields(specs, world)[rank]
+        total = float(sum(shard.field_work(f) for f in specs))
+        return [synth.make_field(w, seed=base, index=j) for j in mine], total
+    return synth.make_field(w, seed=base + 100000 * rank), None
 
 
 REFINE_N, REFINE_STEPS, REFINE_CUT = 4096, 20, 64
@@ -325,20 +342,25 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     wl = WORKLOADS[args.workload]
-    d = field_for(args, rank)
+    d, batch_total = field_for(args, rank, world)
     ds = d if isinstance(d, list) else [d]
     d = ds[0]
     f = d["field"]
     N, H, W = d["frames"].shape
     adds = sum(float(x["frames"].size) * x["field"]["nvx"] * x["field"]["nvy"] for x in ds)
+    # work of the whole job: the batch's total, or one field per rank
+    job_adds = batch_total if batch_total is not None else adds * world
+    scaling = "strong" if batch_total is not None else "weak"
     config = {"workload": f"{args.workload}: {wl['desc']}", "frames": N, "height": H, "width": W,
               "nv": [f["nvx"], f["nvy"]], "storage": args.storage, "shift": args.mode,
               "normalize": bool(args.normalize), "cr_clip": args.cr_clip, "tau": f["snr_threshold"],
-              "tile": args.tile, "l2": "inputs larger than L2 (frame cube > 129 MB)"}
-    if len(ds) > 1:
-        config.update({"fields": len(ds), "frames": [x["frames"].shape[0] for x in ds],
+              "tile": args.tile, "graph": bool(args.graph),
+              "l2": "inputs larger than L2 (frame cube > 129 MB)"}
+    if batch_total is not None:
+        config.update({"fields": BATCH, "fields_this_rank": len(ds),
+                       "frames": [x["frames"].shape[0] for x in ds],
                        "sizes": [x["frames"].shape[1] for x in ds],
-                       "nv": [x["field"]["nvx"] for x in ds], "adds_per_step": adds})
+                       "nv": [x["field"]["nvx"] for x in ds], "adds_per_step": batch_total})
 
     if args.impl == "reference":
         if rank != 0:
@@ -377,9 +399,11 @@ def main():
     frames = [torch.from_numpy(x["frames"]).to(dev) for x in ds]
     times = [x["times"] for x in ds]
     stream = torch.cuda.current_stream(dev)
-    plan = st.Plan([x["field"] for x in ds], storage=args.storage, mode=args.mode, normalize=bool(args.normalize),
-                   cr_clip=args.cr_clip if args.normalize else 0.0, tile=args.tile,
-                   pending_capacity=1 << 24, stream=stream)
+    plan = st.Plan([x["field"] for x in ds], storage=args.storage, mode=args.mode,
+                   normalize=bool(args.normalize), cr_clip=args.cr_clip if args.normalize else 0.0,
+                   tile=args.tile, use_graph=bool(args.graph),
+                   pending_capacity=(1 << 27) if batch_total is not None else (1 << 24),
+                   stream=stream)
     cap = 1 << 22
     out = torch.empty((cap, 7), dtype=torch.int32, device=dev)
 
@@ -416,7 +440,7 @@ def main():
         tt = torch.tensor([t_step], device=dev)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         t_step = float(tt.item())
-    value = adds * world / t_step / 1e9
+    value = job_adds / t_step / 1e9
 
     # end to end through the host-buffer entry point (pinned frames)
     e2e = None
@@ -448,7 +472,7 @@ def main():
             tt = torch.tensor([te], device=dev)
             torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
             te = float(tt.item())
-        e2e = {"value": adds * world / te / 1e9, "unit": "G adds/s",
+        e2e = {"value": job_adds / te / 1e9, "unit": "G adds/s",
                "h2d_bytes_per_step": int(sum(h.numel() * 4 for h in hframes) +
                                          sum(t_.nbytes for t_ in tarr)),
                "d2h_bytes_per_step": int(nh * 28 + 32), "s_per_step": te}
@@ -480,12 +504,14 @@ def main():
                "sample": sample, "seconds": el}
     if e2e:
         e2e["unit"] = unit
+    if args.graph:
+        config["graph_replayed"] = plan.last_graph_replayed()
     line = {
         "metric": METRIC, "value": value, "unit": unit, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": scaling, "vs_baseline": None, "dtype": "f32",
         "data": "synthetic", "config": config,
-        "fields_per_hr": 3600.0 / t_step * world * len(ds),
+        "fields_per_hr": 3600.0 / t_step * (BATCH if batch_total is not None else world),
         "candidates": int(n_found), "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
         "e2e": e2e, "gpu_launches": int(launches), "device": props.name}
     print(json.dumps(line))

@@ -184,16 +184,8 @@ def make_field(name, seed=None, **kw):
                     n_cosmics=int(hits))
     if name == "batched":
         j = kw.get("index", 0)
-        rng = np.random.Generator(np.random.Philox(seed + 1000 * j))
-        N = int(kw.get("n_frames", rng.integers(40, 401)))
-        W = H = int(kw.get("width", rng.choice([512, 1024, 2048])))
-        B = float(kw.get("baseline", rng.uniform(1.0, 8.0)))
-        t = np.linspace(0.0, B, N)
-        t_ref = float(t[N // 2])
-        dv = 1.0 / B
-        nv = int(kw.get("nv", 2 * int(math.floor(60.0 * B)) + 1))
-        f = field_params(W, H, N, t_ref, -dv * (nv // 2), dv, nv, -dv * (nv // 2), dv, nv,
-                         kw.get("tau", 5.0))
+        rng, f, t, B = _batched_params(seed, j, kw)
+        N, H, W, t_ref = f["n_frames"], f["height"], f["width"], f["t_ref"]
         frames = noise(N, H, W, seed + 1000 * j)
         M = int(kw.get("n_movers", rng.integers(10, 81)))
         truth = _place_movers(rng, M, W, H, t, t_ref, lambda r: r.uniform(0.0, 60.0),
@@ -201,6 +193,26 @@ def make_field(name, seed=None, **kw):
         render_movers(frames, t, t_ref, truth, fwhm)
         return dict(field=f, frames=frames, times=t, truth=truth, unit="h", fwhm=fwhm)
     raise ValueError(f"unknown workload {name!r}")
+
+
+def _batched_params(seed, j, kw):
+    rng = np.random.Generator(np.random.Philox(seed + 1000 * j))
+    N = int(kw.get("n_frames", rng.integers(40, 401)))
+    W = H = int(kw.get("width", rng.choice([512, 1024, 2048])))
+    B = float(kw.get("baseline", rng.uniform(1.0, 8.0)))
+    t = np.linspace(0.0, B, N)
+    t_ref = float(t[N // 2])
+    dv = 1.0 / B
+    nv = int(kw.get("nv", 2 * int(math.floor(60.0 * B)) + 1))
+    f = field_params(W, H, N, t_ref, -dv * (nv // 2), dv, nv, -dv * (nv // 2), dv, nv,
+                     kw.get("tau", 5.0))
+    return rng, f, t, B
+
+
+def batched_field(seed, index):
+    """Parameters of field `index` of the batched workload (no frames drawn),
+    identical to make_field("batched", seed=seed, index=index)["field"]."""
+    return _batched_params(seed, index, {})[1]
 
 
 def velocity_index(field, vx, vy):
