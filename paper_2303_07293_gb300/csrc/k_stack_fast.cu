@@ -253,6 +253,17 @@ __device__ __forceinline__ void add_pattern(float2 (&acc)[kMB][KY / 2], const fl
   add_column<KY, pat_off(ID, 3)>(acc[3], w, std::make_integer_sequence<int, KY / 2>{});
 }
 
+// Column pairs: the thread's two columns (c and c + 32) share every row
+// offset, so window row r of both is one register pair and every add is a
+// paired add: acc[j][r] += (wA[r + c_j], wB[r + c_j]).
+template <int KY, int ID>
+__device__ __forceinline__ void add_pattern_cp(float2 (&acc)[kMB][KY], const float2 (&w)[KY + 3]) {
+#pragma unroll
+  for (int j = 0; j < kMB; ++j)
+#pragma unroll
+    for (int r = 0; r < KY; ++r) acc[j][r] = __fadd2_rn(acc[j][r], w[r + pat_off(ID, j)]);
+}
+
 // Bilinear: for the 4 y-velocities, acc[j][row] gets one sample per output
 // row, as four fused multiply-adds in the generic kernel's order
 // (bilinear_acc), with taps from the window rows r + c_j and r + c_j + 1 of
@@ -316,22 +327,26 @@ struct Item {
   int f;           // index into the launch's field list (-1: no more work)
   int X0, Y0, A, B;
 };
-// Items of a field for tile height ky: super-tiles x 16 tiles x velocity tiles.
-__device__ __host__ __forceinline__ int super_x_of(int W) { return ((W + kTX - 1) / kTX + kSuper - 1) / kSuper; }
-__device__ __host__ __forceinline__ int64_t items_of(const FastField& ff, int ky) {
-  const int sy = ((ff.H + ky - 1) / ky + kSuper - 1) / kSuper;
-  return (int64_t)super_x_of(ff.W) * sy * kSuper * kSuper * ff.nA * ff.nB;
+// Items of a field for tile height ky and width tx: super-tiles x 16 tiles x
+// velocity tiles.
+__device__ __host__ __forceinline__ int super_x_of(int W, int tx) {
+  return ((W + tx - 1) / tx + kSuper - 1) / kSuper;
 }
-__device__ __forceinline__ Item decode_item(const FastField& ff, int f, int64_t L, int ky) {
+__device__ __host__ __forceinline__ int64_t items_of(const FastField& ff, int ky, int tx) {
+  const int sy = ((ff.H + ky - 1) / ky + kSuper - 1) / kSuper;
+  return (int64_t)super_x_of(ff.W, tx) * sy * kSuper * kSuper * ff.nA * ff.nB;
+}
+__device__ __forceinline__ Item decode_item(const FastField& ff, int f, int64_t L, int ky,
+                                            int tx) {
   const int nVT = ff.nA * ff.nB;
-  const int super_x = super_x_of(ff.W);
+  const int super_x = super_x_of(ff.W, tx);
   const int sub = (int)(L % (kSuper * kSuper));
   const int64_t rest = L / (kSuper * kSuper);
   const int vt = (int)(rest % nVT);
   const int stile = (int)(rest / nVT);
   Item it;
   it.f = f;
-  it.X0 = ((stile % super_x) * kSuper + sub % kSuper) * kTX;
+  it.X0 = ((stile % super_x) * kSuper + sub % kSuper) * tx;
   it.Y0 = ((stile / super_x) * kSuper + sub / kSuper) * ky;
   it.A = vt % ff.nA;
   it.B = vt / ff.nA;
@@ -356,15 +371,18 @@ __device__ __forceinline__ void tmap_acquire(const CUtensorMap* m) {
 // item's count of fully-inside frames in shared memory.  Warps 0..7 consume.
 // A ring of S stages runs continuously across items and fields; when the
 // work runs out the producer publishes an end item.  Every wait is bounded.
-template <typename T, int KY, int S, int F, bool DUMP, bool BL>
+template <typename T, int KY, int S, int F, bool DUMP, bool BL, bool CP>
 __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
     k_stack_fast(const __grid_constant__ FastArgs p) {
-  constexpr int kBoxW = Store<T>::kBoxW;
+  static_assert(!(CP && BL), "column pairs are built for nearest sampling");
+  constexpr int kTXv = CP ? 2 * kTX : kTX;  // tile width: one or two columns per lane
+  constexpr int kBoxW = Store<T>::kBoxW + (CP ? kTX : 0);
+  constexpr int kAccN = CP ? KY : KY / 2;   // paired accumulators per y-velocity
   constexpr int kTY = KY;         // tile height: one row group of KY rows per thread
   constexpr int kBoxH = KY + 3 + (BL ? 1 : 0);  // tile rows + staircase offset (+ lower tap)
   constexpr int kEdge = BL ? 1 : 0;  // a bilinear sample also reads the next column / row
   constexpr int kCW = kXV;        // consumer warps
-  constexpr int kOut = kMB * KY;  // outputs per thread per item
+  constexpr int kOut = kMB * KY * (CP ? 2 : 1);  // outputs per thread per item
   constexpr int kItemSlots = 8;
   constexpr int kNoop = kPatterns;  // pattern id of a padding frame
   static_assert(F <= 4, "pattern ids of a stage are packed into one word");
@@ -403,7 +421,7 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
     // ------------------------------------------------------------ producer
     int slot = 0, f = 0, acq_f = -1;
     int64_t base = 0;                        // first item of field f
-    int64_t f_items = items_of(*p.ff[0], KY);  // items of field f
+    int64_t f_items = items_of(*p.ff[0], KY, kTXv);  // items of field f
     int64_t seq = 0;  // stages issued
     bool ok = true;
     for (int item = 0; ok; ++item) {
@@ -414,11 +432,11 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
       // the field of item L (items are taken in increasing order)
       while (!done && L >= base + f_items) {
         base += f_items;
-        f_items = items_of(*p.ff[++f], KY);
+        f_items = items_of(*p.ff[++f], KY, kTXv);
       }
       const FastField& ff = *p.ff[f];
       Item it{-1, 0, 0, 0, 0};
-      if (!done) it = decode_item(ff, f, L - base, KY);
+      if (!done) it = decode_item(ff, f, L - base, KY, kTXv);
       const CUtensorMap* map = p.maps[f];
       if (!done && f != acq_f) {
         if (lane == 0) {
@@ -458,7 +476,7 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
             }
             // every sample of the item strictly inside (bilinear: with its
             // right and lower taps), so every output of the item is covered
-            const bool inside = it.X0 + xe.z >= 0 && it.X0 + kTX - 1 + xe.w + kEdge < ff.W &&
+            const bool inside = it.X0 + xe.z >= 0 && it.X0 + kTXv - 1 + xe.w + kEdge < ff.W &&
                                 it.Y0 + ye.x >= 0 && it.Y0 + kTY - 1 + ye.y + kEdge < ff.H;
             if (inside) atomicAdd(&item_inside[item % kItemSlots], 1);
             tma_load_3d(smem + (size_t)(slot * F + lane) * box_floats, map, it.X0 + xe.x,
@@ -502,11 +520,11 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
     const FastField& ff = *p.ff[it.f];
     const int N = ff.N;
     const int spi = (N + F - 1) / F;
-    float2 acc[kMB][KY / 2];
+    float2 acc[kMB][kAccN];
 #pragma unroll
     for (int j = 0; j < kMB; ++j)
 #pragma unroll
-      for (int m = 0; m < KY / 2; ++m) acc[j][m] = make_float2(0.0f, 0.0f);
+      for (int m = 0; m < kAccN; ++m) acc[j][m] = make_float2(0.0f, 0.0f);
 
     bool ok = true;
     for (int st = 0; st < spi; ++st) {
@@ -558,6 +576,34 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
             case kNoop: break;  // padding frame
             default: __builtin_unreachable();
           }
+        } else if constexpr (CP) {
+          float2 wp[KY + 3];  // rows of columns c and c + 32: register pairs
+#pragma unroll
+          for (int r = 0; r < KY + 3; ++r)
+            wp[r] = make_float2(Store<T>::f(col[r * kBoxW]), Store<T>::f(col[r * kBoxW + kTX]));
+          if (fi == F - 1) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty_bar[c_slot]);
+          }
+          switch (id) {
+            case 0: add_pattern_cp<KY, 0>(acc, wp); break;
+            case 1: add_pattern_cp<KY, 1>(acc, wp); break;
+            case 2: add_pattern_cp<KY, 2>(acc, wp); break;
+            case 3: add_pattern_cp<KY, 3>(acc, wp); break;
+            case 4: add_pattern_cp<KY, 4>(acc, wp); break;
+            case 5: add_pattern_cp<KY, 5>(acc, wp); break;
+            case 6: add_pattern_cp<KY, 6>(acc, wp); break;
+            case 7: add_pattern_cp<KY, 7>(acc, wp); break;
+            case 8: add_pattern_cp<KY, 8>(acc, wp); break;
+            case 9: add_pattern_cp<KY, 9>(acc, wp); break;
+            case 10: add_pattern_cp<KY, 10>(acc, wp); break;
+            case 11: add_pattern_cp<KY, 11>(acc, wp); break;
+            case 12: add_pattern_cp<KY, 12>(acc, wp); break;
+            case 13: add_pattern_cp<KY, 13>(acc, wp); break;
+            case 14: add_pattern_cp<KY, 14>(acc, wp); break;
+            case kNoop: break;  // padding frame
+            default: __builtin_unreachable();
+          }
         } else {
           float w[KY + 3];
 #pragma unroll
@@ -599,83 +645,161 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
     const int n_full = item_inside[item % kItemSlots];
     const int x = it.X0 + lane;
     const int av = it.A * kXV + xw;
-    if constexpr (DUMP) {
-#pragma unroll
-      for (int j = 0; j < kMB; ++j)
-#pragma unroll
-        for (int m = 0; m < KY / 2; ++m)
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int bv = it.B * kMB + j, y = it.Y0 + 2 * m + h;
-            if (x < ff.W && y < ff.H && av < ff.nvx && bv < ff.nvy) {
-              const int64_t o =
-                  ((int64_t)bv * ff.nvx + av) * ff.W * (int64_t)ff.H + (int64_t)y * ff.W + x;
-              p.dump_S[o] = h == 0 ? acc[j][m].x : acc[j][m].y;
-              if (p.dump_C)
-                p.dump_C[o] = BL ? exact_coverage_bl(ff, x, y, av, bv)
-                                 : exact_coverage(ff, x, y, av, bv);
-            }
-          }
-    } else {
-      // outputs at or above the block's lowest possible threshold, as a
-      // bitmask; the exact coverage, threshold and local-maximum test of
-      // these rare points happen in the resolver
-      constexpr int kWords = (kOut + 31) / 32;
-      uint32_t mask[kWords];
-#pragma unroll
-      for (int b = 0; b < kWords; ++b) mask[b] = 0u;
-      if (n_full == N) {
-        // interior item: every output is covered by all N frames
-        const float thr_n = __ldg(ff.thr + max(N, ff.nmin));
+    if constexpr (CP) {
+      // outputs (j, r, h): y-velocity j, row r, column x + 32 h; value
+      // acc[j][r].x (h = 0) or .y (h = 1); bit o = (j KY + r) 2 + h
+      if constexpr (DUMP) {
 #pragma unroll
         for (int j = 0; j < kMB; ++j)
 #pragma unroll
-          for (int m = 0; m < KY / 2; ++m) {
-            const int o = j * KY + 2 * m;
-            mask[o / 32] |= (uint32_t)(acc[j][m].x >= thr_n) << (o % 32);
-            mask[o / 32] |= (uint32_t)(acc[j][m].y >= thr_n) << (o % 32 + 1);
-          }
+          for (int r = 0; r < KY; ++r)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int bv = it.B * kMB + j, y = it.Y0 + r, xh = x + kTX * h;
+              if (xh < ff.W && y < ff.H && av < ff.nvx && bv < ff.nvy) {
+                const int64_t o =
+                    ((int64_t)bv * ff.nvx + av) * ff.W * (int64_t)ff.H + (int64_t)y * ff.W + xh;
+                p.dump_S[o] = h == 0 ? acc[j][r].x : acc[j][r].y;
+                if (p.dump_C) p.dump_C[o] = exact_coverage(ff, xh, y, av, bv);
+              }
+            }
       } else {
-        // edge item: n_cov >= nx + ny - N, with nx / ny the frames whose x / y
-        // sample is inside (bilinear: with its right / lower tap, which
-        // implies inside for any fraction; ny taken at the item's least
-        // covered row), and n_cov >= n_full; thresholds grow with n_cov, so
-        // this never drops a candidate
-        const int avc = min(av, ff.nvx - 1);
-        const int nx = count_shifts(ff.covx + (int64_t)avc * ff.cov_len,
-                                    __ldg(ff.cov_xmin + avc), __ldg(ff.cov_xmax + avc), N, -x,
-                                    ff.W - 1 - kEdge - x);
+        constexpr int kWords = (kOut + 31) / 32;
+        uint32_t mask[kWords];
 #pragma unroll
-        for (int j = 0; j < kMB; ++j) {
-          // ny minimised over the item's rows (lane l takes row l % KY)
-          const int bvc = min(it.B * kMB + j, ff.nvy - 1);
-          const int y = it.Y0 + lane % KY;
-          int ny = count_shifts(ff.covy + (int64_t)bvc * ff.cov_len, __ldg(ff.cov_ymin + bvc),
-                                __ldg(ff.cov_ymax + bvc), N, -y, ff.H - 1 - kEdge - y);
+        for (int b = 0; b < kWords; ++b) mask[b] = 0u;
+        const bool ok0 = x < ff.W && av < ff.nvx, ok1 = x + kTX < ff.W && av < ff.nvx;
+        if (n_full == N) {
+          const float thr_n = __ldg(ff.thr + max(N, ff.nmin));
 #pragma unroll
-          for (int d = 16; d > 0; d >>= 1) ny = min(ny, __shfl_xor_sync(0xffffffffu, ny, d));
-          const int nlo = max(max(n_full, ff.nmin), nx + ny - N);
-          const float thr_j = __ldg(ff.thr + min(nlo, N));
+          for (int j = 0; j < kMB; ++j)
 #pragma unroll
-          for (int m = 0; m < KY / 2; ++m) {
-            const int o = j * KY + 2 * m;
-            mask[o / 32] |= (uint32_t)(acc[j][m].x >= thr_j) << (o % 32);
-            mask[o / 32] |= (uint32_t)(acc[j][m].y >= thr_j) << (o % 32 + 1);
+            for (int r = 0; r < KY; ++r) {
+              const int o = (j * KY + r) * 2;
+              mask[o / 32] |= (uint32_t)(ok0 && acc[j][r].x >= thr_n) << (o % 32);
+              mask[o / 32] |= (uint32_t)(ok1 && acc[j][r].y >= thr_n) << (o % 32 + 1);
+            }
+        } else {
+          // edge item: as for single columns, with nx per column
+          const int avc = min(av, ff.nvx - 1);
+          const int* px = ff.covx + (int64_t)avc * ff.cov_len;
+          const int sxmin = __ldg(ff.cov_xmin + avc), sxmax = __ldg(ff.cov_xmax + avc);
+          const int nx0 = count_shifts(px, sxmin, sxmax, N, -x, ff.W - 1 - kEdge - x);
+          const int nx1 =
+              count_shifts(px, sxmin, sxmax, N, -(x + kTX), ff.W - 1 - kEdge - (x + kTX));
+#pragma unroll
+          for (int j = 0; j < kMB; ++j) {
+            const int bvc = min(it.B * kMB + j, ff.nvy - 1);
+            const int y = it.Y0 + lane % KY;
+            int ny = count_shifts(ff.covy + (int64_t)bvc * ff.cov_len, __ldg(ff.cov_ymin + bvc),
+                                  __ldg(ff.cov_ymax + bvc), N, -y, ff.H - 1 - kEdge - y);
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) ny = min(ny, __shfl_xor_sync(0xffffffffu, ny, d));
+            const int base = max(n_full, ff.nmin);
+            const float thr0 = __ldg(ff.thr + min(max(base, nx0 + ny - N), N));
+            const float thr1 = __ldg(ff.thr + min(max(base, nx1 + ny - N), N));
+#pragma unroll
+            for (int r = 0; r < KY; ++r) {
+              const int o = (j * KY + r) * 2;
+              mask[o / 32] |= (uint32_t)(ok0 && acc[j][r].x >= thr0) << (o % 32);
+              mask[o / 32] |= (uint32_t)(ok1 && acc[j][r].y >= thr1) << (o % 32 + 1);
+            }
+          }
+        }
+        for (int b = 0; b < kWords; ++b) {
+          uint32_t mk = mask[b];
+          while (__any_sync(0xffffffffu, mk != 0u)) {
+            const bool has = mk != 0u;
+            const int bit = has ? __ffs(mk) - 1 : 0;
+            mk &= has ? mk - 1u : 0u;
+            const int o = b * 32 + bit;
+            const int j = o / (2 * KY), y = it.Y0 + (o >> 1) % KY, bv = it.B * kMB + j;
+            const int xh = x + kTX * (o & 1);
+            const bool valid = has && y < ff.H && bv < ff.nvy;
+            Pending rec{xh, y, bv * ff.nvx + av, ff.field, 0.0f, -1};
+            push_pending(valid, rec, p.pend, p.cap, p.ctr);
           }
         }
       }
-      const bool col_ok = x < ff.W && av < ff.nvx;
-      for (int b = 0; b < kWords; ++b) {
-        uint32_t mk = col_ok ? mask[b] : 0u;
-        while (__any_sync(0xffffffffu, mk != 0u)) {
-          const bool has = mk != 0u;
-          const int bit = has ? __ffs(mk) - 1 : 0;
-          mk &= has ? mk - 1u : 0u;
-          const int o = b * 32 + bit;
-          const int j = o / KY, y = it.Y0 + o % KY, bv = it.B * kMB + j;
-          const bool valid = has && y < ff.H && bv < ff.nvy;
-          Pending rec{x, y, bv * ff.nvx + av, ff.field, 0.0f, -1};
-          push_pending(valid, rec, p.pend, p.cap, p.ctr);
+    } else {
+      if constexpr (DUMP) {
+  #pragma unroll
+        for (int j = 0; j < kMB; ++j)
+  #pragma unroll
+          for (int m = 0; m < KY / 2; ++m)
+  #pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int bv = it.B * kMB + j, y = it.Y0 + 2 * m + h;
+              if (x < ff.W && y < ff.H && av < ff.nvx && bv < ff.nvy) {
+                const int64_t o =
+                    ((int64_t)bv * ff.nvx + av) * ff.W * (int64_t)ff.H + (int64_t)y * ff.W + x;
+                p.dump_S[o] = h == 0 ? acc[j][m].x : acc[j][m].y;
+                if (p.dump_C)
+                  p.dump_C[o] = BL ? exact_coverage_bl(ff, x, y, av, bv)
+                                   : exact_coverage(ff, x, y, av, bv);
+              }
+            }
+      } else {
+        // outputs at or above the block's lowest possible threshold, as a
+        // bitmask; the exact coverage, threshold and local-maximum test of
+        // these rare points happen in the resolver
+        constexpr int kWords = (kOut + 31) / 32;
+        uint32_t mask[kWords];
+  #pragma unroll
+        for (int b = 0; b < kWords; ++b) mask[b] = 0u;
+        if (n_full == N) {
+          // interior item: every output is covered by all N frames
+          const float thr_n = __ldg(ff.thr + max(N, ff.nmin));
+  #pragma unroll
+          for (int j = 0; j < kMB; ++j)
+  #pragma unroll
+            for (int m = 0; m < KY / 2; ++m) {
+              const int o = j * KY + 2 * m;
+              mask[o / 32] |= (uint32_t)(acc[j][m].x >= thr_n) << (o % 32);
+              mask[o / 32] |= (uint32_t)(acc[j][m].y >= thr_n) << (o % 32 + 1);
+            }
+        } else {
+          // edge item: n_cov >= nx + ny - N, with nx / ny the frames whose x / y
+          // sample is inside (bilinear: with its right / lower tap, which
+          // implies inside for any fraction; ny taken at the item's least
+          // covered row), and n_cov >= n_full; thresholds grow with n_cov, so
+          // this never drops a candidate
+          const int avc = min(av, ff.nvx - 1);
+          const int nx = count_shifts(ff.covx + (int64_t)avc * ff.cov_len,
+                                      __ldg(ff.cov_xmin + avc), __ldg(ff.cov_xmax + avc), N, -x,
+                                      ff.W - 1 - kEdge - x);
+  #pragma unroll
+          for (int j = 0; j < kMB; ++j) {
+            // ny minimised over the item's rows (lane l takes row l % KY)
+            const int bvc = min(it.B * kMB + j, ff.nvy - 1);
+            const int y = it.Y0 + lane % KY;
+            int ny = count_shifts(ff.covy + (int64_t)bvc * ff.cov_len, __ldg(ff.cov_ymin + bvc),
+                                  __ldg(ff.cov_ymax + bvc), N, -y, ff.H - 1 - kEdge - y);
+  #pragma unroll
+            for (int d = 16; d > 0; d >>= 1) ny = min(ny, __shfl_xor_sync(0xffffffffu, ny, d));
+            const int nlo = max(max(n_full, ff.nmin), nx + ny - N);
+            const float thr_j = __ldg(ff.thr + min(nlo, N));
+  #pragma unroll
+            for (int m = 0; m < KY / 2; ++m) {
+              const int o = j * KY + 2 * m;
+              mask[o / 32] |= (uint32_t)(acc[j][m].x >= thr_j) << (o % 32);
+              mask[o / 32] |= (uint32_t)(acc[j][m].y >= thr_j) << (o % 32 + 1);
+            }
+          }
+        }
+        const bool col_ok = x < ff.W && av < ff.nvx;
+        for (int b = 0; b < kWords; ++b) {
+          uint32_t mk = col_ok ? mask[b] : 0u;
+          while (__any_sync(0xffffffffu, mk != 0u)) {
+            const bool has = mk != 0u;
+            const int bit = has ? __ffs(mk) - 1 : 0;
+            mk &= has ? mk - 1u : 0u;
+            const int o = b * 32 + bit;
+            const int j = o / KY, y = it.Y0 + o % KY, bv = it.B * kMB + j;
+            const bool valid = has && y < ff.H && bv < ff.nvy;
+            Pending rec{x, y, bv * ff.nvx + av, ff.field, 0.0f, -1};
+            push_pending(valid, rec, p.pend, p.cap, p.ctr);
+          }
         }
       }
     }
@@ -696,27 +820,32 @@ struct Variant {
   void (*fn)(FastArgs);
   void (*dump_fn)(FastArgs);
   int threads, stages, ky, stages_f;
+  int tx;  // tile width: 32 (one column per lane) or 64 (column pairs)
   const char* name;
 };
 
-#define ST_VARIANT(T, KY, S, F, BL)                                                           \
+#define ST_VARIANT(T, KY, S, F, BL, CP)                                                       \
   {                                                                                           \
-    (void (*)(FastArgs))k_stack_fast<T, KY, S, F, false, BL>,                                   \
-        (void (*)(FastArgs))k_stack_fast<T, KY, S, F, true, BL>, 32 * (kXV + 1),               \
-        S * F, KY, F, #T "_ky" #KY "_s" #S "_f" #F                                             \
+    (void (*)(FastArgs))k_stack_fast<T, KY, S, F, false, BL, CP>,                               \
+        (void (*)(FastArgs))k_stack_fast<T, KY, S, F, true, BL, CP>, 32 * (kXV + 1), S * F,    \
+        KY, F, CP ? 2 * kTX : kTX, #T "_ky" #KY "_s" #S "_f" #F #CP                            \
   }
-const Variant kVarF32[] = {ST_VARIANT(float, 16, 6, 4, false), ST_VARIANT(float, 16, 8, 4, false),
-                           ST_VARIANT(float, 20, 6, 4, false), ST_VARIANT(float, 24, 6, 4, false),
-                           ST_VARIANT(float, 16, 12, 2, false)};
-const Variant kVarF16[] = {ST_VARIANT(__half, 16, 6, 4, false),
-                           ST_VARIANT(__half, 16, 8, 4, false)};
-const Variant kVarBF16[] = {ST_VARIANT(__nv_bfloat16, 16, 6, 4, false),
-                            ST_VARIANT(__nv_bfloat16, 16, 8, 4, false)};
+#define NEAR(T, KY, S, F) ST_VARIANT(T, KY, S, F, false, false)
+#define PAIR(T, KY, S, F) ST_VARIANT(T, KY, S, F, false, true)
+#define BILI(T, KY, S, F) ST_VARIANT(T, KY, S, F, true, false)
+const Variant kVarF32[] = {NEAR(float, 16, 6, 4), NEAR(float, 16, 8, 4), NEAR(float, 20, 6, 4),
+                           NEAR(float, 24, 6, 4), NEAR(float, 16, 12, 2), PAIR(float, 8, 8, 4)};
+const Variant kVarF16[] = {NEAR(__half, 16, 6, 4), NEAR(__half, 16, 8, 4),
+                           PAIR(__half, 8, 8, 4)};
+const Variant kVarBF16[] = {NEAR(__nv_bfloat16, 16, 6, 4), NEAR(__nv_bfloat16, 16, 8, 4),
+                            PAIR(__nv_bfloat16, 8, 8, 4)};
 // bilinear sampling: two window columns and 4 weights per y-velocity
-const Variant kVarBlF32[] = {ST_VARIANT(float, 8, 8, 4, true), ST_VARIANT(float, 10, 8, 4, true),
-                             ST_VARIANT(float, 8, 12, 4, true)};
-const Variant kVarBlF16[] = {ST_VARIANT(__half, 8, 8, 4, true)};
-const Variant kVarBlBF16[] = {ST_VARIANT(__nv_bfloat16, 8, 8, 4, true)};
+const Variant kVarBlF32[] = {BILI(float, 8, 8, 4), BILI(float, 10, 8, 4), BILI(float, 8, 12, 4)};
+const Variant kVarBlF16[] = {BILI(__half, 8, 8, 4)};
+const Variant kVarBlBF16[] = {BILI(__nv_bfloat16, 8, 8, 4)};
+#undef NEAR
+#undef PAIR
+#undef BILI
 #undef ST_VARIANT
 constexpr int kNumVariants = sizeof(kVarF32) / sizeof(kVarF32[0]);  // the largest list
 
@@ -782,6 +911,7 @@ struct FastPlan {
   CUtensorMap tmap;
   const void* encoded_for = nullptr;
   int encoded_boxh = 0;
+  int encoded_boxw = 0;
   int variant = 0;         // index into the (storage type, sampling) variant list
   bool bl = false;         // bilinear sampling
   int64_t item_limit = 0;  // > 0: run only the first item_limit items (autotuning)
@@ -1028,17 +1158,20 @@ static const Variant* stage_maps(const FieldDev* fds, FastPlan* const* fps, int 
   const int vi = fp0->variant < nvar ? fp0->variant : 0;
   const Variant& var = vars[vi];
   const int boxh = var.ky + 3 + (fp0->bl ? 1 : 0);
-  const int boxw = fds[0].storage == ST_F32 ? Store<float>::kBoxW : Store<__half>::kBoxW;
+  const int boxw = (fds[0].storage == ST_F32 ? Store<float>::kBoxW : Store<__half>::kBoxW) +
+                   (var.tx - kTX);
   for (int i = 0; i < n; ++i) {
     FastPlan* fp = fps[i];
     if (fds[i].storage != fds[0].storage || fp->bl != fp0->bl) return nullptr;
-    if (fp->encoded_for != fds[i].cube || fp->encoded_boxh != boxh) {
+    if (fp->encoded_for != fds[i].cube || fp->encoded_boxh != boxh ||
+        fp->encoded_boxw != boxw) {
       if (!encode_tile_map(&fp->tmap, fds[i], boxw, boxh)) return nullptr;
       if (cudaMemcpyAsync(fp->d_map, &fp->tmap, sizeof(CUtensorMap), cudaMemcpyHostToDevice,
                           s) != cudaSuccess)
         return nullptr;
       fp->encoded_for = fds[i].cube;
       fp->encoded_boxh = boxh;
+      fp->encoded_boxw = boxw;
       if (restaged) *restaged = true;
     }
   }
@@ -1069,7 +1202,8 @@ int launch_stack_fast_multi(const FieldDev* fds, FastPlan* const* fps, int n, fl
   if (!vp) return -1;
   const Variant& var = *vp;
   const int ky = var.ky, boxh = ky + 3 + (fp0->bl ? 1 : 0);
-  const int boxw = fds[0].storage == ST_F32 ? Store<float>::kBoxW : Store<__half>::kBoxW;
+  const int boxw = (fds[0].storage == ST_F32 ? Store<float>::kBoxW : Store<__half>::kBoxW) +
+                   (var.tx - kTX);
   // fields longest first (the items of the most frames are taken first)
   int order[kMaxFields];
   for (int i = 0; i < n; ++i) order[i] = i;
@@ -1080,7 +1214,7 @@ int launch_stack_fast_multi(const FieldDev* fds, FastPlan* const* fps, int n, fl
   for (int i = 0; i < n; ++i) {
     a.ff[i] = fps[order[i]]->d_ff;
     a.maps[i] = fps[order[i]]->d_map;
-    total += items_of(fps[order[i]]->h_ff, ky);
+    total += items_of(fps[order[i]]->h_ff, ky, var.tx);
   }
   a.n_fields = n;
   a.n_items = fp0->item_limit > 0 && total > fp0->item_limit ? fp0->item_limit : total;

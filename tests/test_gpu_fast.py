@@ -25,7 +25,7 @@ def st():
     return m
 
 
-VARIANTS = [0, 2, 3, 4, 5, 6]   # plan default and every register-window variant
+VARIANTS = [0, 2, 3, 4, 5, 6, 7]   # plan default and every register-window variant
 
 
 def dev(a):
@@ -102,7 +102,7 @@ def test_fast_reduced_storage_bitexact_on_rounded_frames(st, storage):
     ks = np.arange(f["nvx"] * f["nvy"], dtype=np.int32)
     oS, oC = oracle.stack_planes(rounded, t, f, ks, prec="fp32")
     ref = oracle.search(rounded, t, f, prec="fp32")
-    for tile in (0, 2, 3):
+    for tile in (0, 2, 3, 4):   # 4: column pairs
         with st.Plan(f, storage=storage, tile=tile) as p:
             S, Cv = p.dump_stack(0, dev(fr), t, ks)
             got = p.candidates(dev(fr), t)
