@@ -37,6 +37,22 @@ WORKLOADS = {
 }
 METRIC = "G pixel*frame*velocity adds/s (2048x2048x256, 801x801 grid)"
 
+# DRAM bytes (read + write) of one stack-kernel launch, from one ncu capture
+# of `--metrics dram__bytes_read.sum,dram__bytes_write.sum` (profiles/
+# stack_speculoos_2048x256_traffic.md), with the SHA-1 prefix of
+# k_stack_fast.cu it was taken on: reported only while the source is that one.
+STACK_TRAFFIC = {
+    ("speculoos", "f32", "nearest"): (54.27e9 + 374.60e6, "6de40f172f52"),
+    ("mid", "f32", "nearest"): (278.75e6 + 6.60e6, "6de40f172f52"),
+}
+
+
+def stack_source_sha():
+    import hashlib
+    path = os.path.join(ROOT, "paper_2303_07293_gb300", "csrc", "k_stack_fast.cu")
+    with open(path, "rb") as fh:
+        return hashlib.sha1(fh.read()).hexdigest()[:12]
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -140,16 +156,21 @@ def oracle_baseline(d, seconds, mode="nearest"):
     fr = np.nan_to_num(d["frames"], nan=0.0)
     nk = f["nvx"] * f["nvy"]
     k0 = nk // 2 - cores // 2
-    t0 = time.perf_counter()
     prec = "fp64" if mode == "bilinear" else "fp32"
-    oracle.search(fr, d["times"], f, mode=mode, prec=prec, k_begin=k0, k_end=k0 + cores)
-    dt = time.perf_counter() - t0
-    per_round = dt
-    rounds = max(1, int(seconds / max(per_round, 1e-3)) - 1)
-    k1 = min(nk, k0 + cores + rounds * cores)
+    # one untimed round of `cores` planes (thread start-up, caches), then
+    # rounds of planes until the sample has taken `seconds`
     t0 = time.perf_counter()
-    oracle.search(fr, d["times"], f, mode=mode, prec=prec, k_begin=k0 + cores, k_end=k1)
-    el = time.perf_counter() - t0
+    oracle.search(fr, d["times"], f, mode=mode, prec=prec, k_begin=k0, k_end=k0 + cores)
+    # rounds of at least ~0.5 s, so per-call set-up does not count
+    chunk = cores * max(1, int(0.5 / max(time.perf_counter() - t0, 1e-6)))
+    k1 = k0 + cores
+    el = 0.0
+    while el < seconds and k1 < nk:
+        k_next = min(nk, k1 + chunk)
+        t0 = time.perf_counter()
+        oracle.search(fr, d["times"], f, mode=mode, prec=prec, k_begin=k1, k_end=k_next)
+        el += time.perf_counter() - t0
+        k1 = k_next
     n_planes = k1 - (k0 + cores)
     adds = float(W * H * N) * n_planes
     kind = "FP64 bilinear" if mode == "bilinear" else "FP32-sequential nearest"
@@ -404,11 +425,17 @@ def main():
                    tile=args.tile, use_graph=bool(args.graph),
                    pending_capacity=(1 << 27) if batch_total is not None else (1 << 24),
                    stream=stream)
-    cap = 1 << 22
+    cap = (1 << 24) if batch_total is not None else (1 << 22)
     out = torch.empty((cap, 7), dtype=torch.int32, device=dev)
 
     def step():
+        nonlocal cap, out
         _, n, status = plan.search(frames, times, capacity=cap, out=out)
+        if status == st.ST_ERR_OVERFLOW and n > cap:
+            # more candidates than the buffer: grow it (the warm-up absorbs this)
+            cap = int(n * 1.25)
+            out = torch.empty((cap, 7), dtype=torch.int32, device=dev)
+            _, n, status = plan.search(frames, times, capacity=cap, out=out)
         if status != st.ST_OK:
             raise RuntimeError(f"search status {status}")
         return n
@@ -485,12 +512,15 @@ def main():
     max_mhz = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
     peak_t = sms * 128 * max_mhz * 1e6 / 1e12  # FP32 adds (or FMAs) per second, T
     stack_avg_ms = stack_ms / max(stack_launch, 1)
+    tr = STACK_TRAFFIC.get((args.workload, args.storage, args.mode))
+    traffic = tr[0] if tr and tr[1] == stack_source_sha() and stack_launch == args.steps \
+        else None
     # algorithmic work per pixel*frame*velocity: 1 add (nearest), 4 FMA (bilinear)
     per_unit = 4.0 if args.mode == "bilinear" else 1.0
     achieved = per_unit * adds / (stack_ms / 1e3 / args.steps) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_t,
             "unit": "T FMA/s" if args.mode == "bilinear" else "T adds/s",
-            "frac": achieved / peak_t, "traffic": None, "work_per_unit": per_unit,
+            "frac": achieved / peak_t, "traffic": traffic, "work_per_unit": per_unit,
             "kernel": "stack (shift-and-stack + threshold)", "launches_per_step":
                 stack_launch / args.steps, "avg_launch_ms": stack_avg_ms,
             "peak_basis": f"{sms} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz (max SM clock)"}

@@ -264,30 +264,32 @@ __device__ __forceinline__ void add_pattern_cp(float2 (&acc)[kMB][KY], const flo
     for (int r = 0; r < KY; ++r) acc[j][r] = __fadd2_rn(acc[j][r], w[r + pat_off(ID, j)]);
 }
 
-// Bilinear: for the 4 y-velocities, acc[j][row] gets one sample per output
-// row, as four fused multiply-adds in the generic kernel's order
-// (bilinear_acc), with taps from the window rows r + c_j and r + c_j + 1 of
-// the column (c0) and its right neighbour (c1).
-template <int KY, int J, int C>
-__device__ __forceinline__ void add_bl_column(float2 (&acc)[KY / 2], const BW& w,
-                                              const float (&c0)[KY + 4],
-                                              const float (&c1)[KY + 4]) {
+// Bilinear, factored: a warp's x-fraction is common to its 4 y-velocities, so
+// the horizontal interpolation h[r] = c0[r] + fx (c1[r] - c0[r]) of window row
+// r is formed once per frame and shared; y-velocity j then adds
+// (1 - fy_j) h[r + c_j] + fy_j h[r + c_j + 1] to output row r as two fused
+// multiply-adds.  (The generic kernel forms the same bilinear sample as four
+// weighted taps; the two agree to FP32 rounding, and the local-maximum
+// resolver re-forms every reported value with the generic arithmetic.)
+template <int KY, int C>
+__device__ __forceinline__ void add_bl_column(float2 (&acc)[KY / 2], float gy, float fy,
+                                              const float (&h)[KY + 4]) {
 #pragma unroll
   for (int m = 0; m < KY / 2; ++m) {
     const int r = 2 * m + C;
-    acc[m].x = bilinear_acc(acc[m].x, w, c0[r], c1[r], c0[r + 1], c1[r + 1]);
-    acc[m].y = bilinear_acc(acc[m].y, w, c0[r + 1], c1[r + 1], c0[r + 2], c1[r + 2]);
+    acc[m].x = __fmaf_rn(fy, h[r + 1], __fmaf_rn(gy, h[r], acc[m].x));
+    acc[m].y = __fmaf_rn(fy, h[r + 2], __fmaf_rn(gy, h[r + 1], acc[m].y));
   }
 }
 
 template <int KY, int ID>
-__device__ __forceinline__ void add_pattern_bl(float2 (&acc)[kMB][KY / 2], const BW (&w)[kMB],
-                                               const float (&c0)[KY + 4],
-                                               const float (&c1)[KY + 4]) {
-  add_bl_column<KY, 0, pat_off(ID, 0)>(acc[0], w[0], c0, c1);
-  add_bl_column<KY, 1, pat_off(ID, 1)>(acc[1], w[1], c0, c1);
-  add_bl_column<KY, 2, pat_off(ID, 2)>(acc[2], w[2], c0, c1);
-  add_bl_column<KY, 3, pat_off(ID, 3)>(acc[3], w[3], c0, c1);
+__device__ __forceinline__ void add_pattern_bl(float2 (&acc)[kMB][KY / 2], const float (&gy)[kMB],
+                                               const float (&fy)[kMB],
+                                               const float (&h)[KY + 4]) {
+  add_bl_column<KY, pat_off(ID, 0)>(acc[0], gy[0], fy[0], h);
+  add_bl_column<KY, pat_off(ID, 1)>(acc[1], gy[1], fy[1], h);
+  add_bl_column<KY, pat_off(ID, 2)>(acc[2], gy[2], fy[2], h);
+  add_bl_column<KY, pat_off(ID, 3)>(acc[3], gy[3], fy[3], h);
 }
 
 // Number of frames whose shift s satisfies lo <= s <= hi, from a prefix table.
@@ -543,36 +545,37 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
         if (fi + 1 < F) oc_next = slot_ocol[c_slot * F + fi + 1];
         const T* col = stage + fi * box_floats + ((oc >> (4 * xw)) & 15u);
         if constexpr (BL) {
-          float c0[KY + 4], c1[KY + 4];
+          float h[KY + 4];
+          const float fxw = slot_fx[(c_slot * F + fi) * kXV + xw];
 #pragma unroll
           for (int r = 0; r < KY + 4; ++r) {
-            c0[r] = Store<T>::f(col[r * kBoxW]);
-            c1[r] = Store<T>::f(col[r * kBoxW + 1]);
+            const float a0 = Store<T>::f(col[r * kBoxW]), a1 = Store<T>::f(col[r * kBoxW + 1]);
+            h[r] = __fmaf_rn(fxw, __fsub_rn(a1, a0), a0);
           }
-          const float fxw = slot_fx[(c_slot * F + fi) * kXV + xw];
           const float4 fy4 = slot_fy[c_slot * F + fi];
           if (fi == F - 1) {
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty_bar[c_slot]);
           }
-          const BW wt[kMB] = {bilinear_weights(fxw, fy4.x), bilinear_weights(fxw, fy4.y),
-                              bilinear_weights(fxw, fy4.z), bilinear_weights(fxw, fy4.w)};
+          const float fy[kMB] = {fy4.x, fy4.y, fy4.z, fy4.w};
+          const float gy[kMB] = {__fsub_rn(1.0f, fy4.x), __fsub_rn(1.0f, fy4.y),
+                                 __fsub_rn(1.0f, fy4.z), __fsub_rn(1.0f, fy4.w)};
           switch (id) {
-            case 0: add_pattern_bl<KY, 0>(acc, wt, c0, c1); break;
-            case 1: add_pattern_bl<KY, 1>(acc, wt, c0, c1); break;
-            case 2: add_pattern_bl<KY, 2>(acc, wt, c0, c1); break;
-            case 3: add_pattern_bl<KY, 3>(acc, wt, c0, c1); break;
-            case 4: add_pattern_bl<KY, 4>(acc, wt, c0, c1); break;
-            case 5: add_pattern_bl<KY, 5>(acc, wt, c0, c1); break;
-            case 6: add_pattern_bl<KY, 6>(acc, wt, c0, c1); break;
-            case 7: add_pattern_bl<KY, 7>(acc, wt, c0, c1); break;
-            case 8: add_pattern_bl<KY, 8>(acc, wt, c0, c1); break;
-            case 9: add_pattern_bl<KY, 9>(acc, wt, c0, c1); break;
-            case 10: add_pattern_bl<KY, 10>(acc, wt, c0, c1); break;
-            case 11: add_pattern_bl<KY, 11>(acc, wt, c0, c1); break;
-            case 12: add_pattern_bl<KY, 12>(acc, wt, c0, c1); break;
-            case 13: add_pattern_bl<KY, 13>(acc, wt, c0, c1); break;
-            case 14: add_pattern_bl<KY, 14>(acc, wt, c0, c1); break;
+            case 0: add_pattern_bl<KY, 0>(acc, gy, fy, h); break;
+            case 1: add_pattern_bl<KY, 1>(acc, gy, fy, h); break;
+            case 2: add_pattern_bl<KY, 2>(acc, gy, fy, h); break;
+            case 3: add_pattern_bl<KY, 3>(acc, gy, fy, h); break;
+            case 4: add_pattern_bl<KY, 4>(acc, gy, fy, h); break;
+            case 5: add_pattern_bl<KY, 5>(acc, gy, fy, h); break;
+            case 6: add_pattern_bl<KY, 6>(acc, gy, fy, h); break;
+            case 7: add_pattern_bl<KY, 7>(acc, gy, fy, h); break;
+            case 8: add_pattern_bl<KY, 8>(acc, gy, fy, h); break;
+            case 9: add_pattern_bl<KY, 9>(acc, gy, fy, h); break;
+            case 10: add_pattern_bl<KY, 10>(acc, gy, fy, h); break;
+            case 11: add_pattern_bl<KY, 11>(acc, gy, fy, h); break;
+            case 12: add_pattern_bl<KY, 12>(acc, gy, fy, h); break;
+            case 13: add_pattern_bl<KY, 13>(acc, gy, fy, h); break;
+            case 14: add_pattern_bl<KY, 14>(acc, gy, fy, h); break;
             case kNoop: break;  // padding frame
             default: __builtin_unreachable();
           }
@@ -747,9 +750,16 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
         uint32_t mask[kWords];
   #pragma unroll
         for (int b = 0; b < kWords; ++b) mask[b] = 0u;
+        // bilinear: the resolver re-forms each value with the generic
+        // arithmetic, which differs from the factored form by FP32 rounding;
+        // the pre-filter threshold is lowered by a relative 2e-4 of the
+        // threshold's scale so no point is dropped for that reason
+        auto lower = [&](float t) {
+          return BL ? t - 2e-4f * (fabsf(t) + sqrtf((float)N)) : t;
+        };
         if (n_full == N) {
           // interior item: every output is covered by all N frames
-          const float thr_n = __ldg(ff.thr + max(N, ff.nmin));
+          const float thr_n = lower(__ldg(ff.thr + max(N, ff.nmin)));
   #pragma unroll
           for (int j = 0; j < kMB; ++j)
   #pragma unroll
@@ -778,7 +788,7 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
   #pragma unroll
             for (int d = 16; d > 0; d >>= 1) ny = min(ny, __shfl_xor_sync(0xffffffffu, ny, d));
             const int nlo = max(max(n_full, ff.nmin), nx + ny - N);
-            const float thr_j = __ldg(ff.thr + min(nlo, N));
+            const float thr_j = lower(__ldg(ff.thr + min(nlo, N)));
   #pragma unroll
             for (int m = 0; m < KY / 2; ++m) {
               const int o = j * KY + 2 * m;
@@ -839,10 +849,10 @@ const Variant kVarF16[] = {NEAR(__half, 16, 6, 4), NEAR(__half, 16, 8, 4),
                            PAIR(__half, 8, 8, 4)};
 const Variant kVarBF16[] = {NEAR(__nv_bfloat16, 16, 6, 4), NEAR(__nv_bfloat16, 16, 8, 4),
                             PAIR(__nv_bfloat16, 8, 8, 4)};
-// bilinear sampling: two window columns and 4 weights per y-velocity
-const Variant kVarBlF32[] = {BILI(float, 8, 8, 4), BILI(float, 10, 8, 4), BILI(float, 8, 12, 4)};
-const Variant kVarBlF16[] = {BILI(__half, 8, 8, 4)};
-const Variant kVarBlBF16[] = {BILI(__nv_bfloat16, 8, 8, 4)};
+// bilinear sampling: two window columns, one shared horizontal interpolation
+const Variant kVarBlF32[] = {BILI(float, 8, 8, 4), BILI(float, 12, 8, 4), BILI(float, 16, 6, 4)};
+const Variant kVarBlF16[] = {BILI(__half, 8, 8, 4), BILI(__half, 12, 8, 4)};
+const Variant kVarBlBF16[] = {BILI(__nv_bfloat16, 8, 8, 4), BILI(__nv_bfloat16, 12, 8, 4)};
 #undef NEAR
 #undef PAIR
 #undef BILI

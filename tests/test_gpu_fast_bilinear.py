@@ -1,12 +1,15 @@
 """GPU parity of the register-window kernel with bilinear sampling (row a4).
 
-The register-window kernel forms every bilinear sample with the generic
-kernel's arithmetic (weights (1-fx)(1-fy), fx(1-fy), (1-fx)fy, fx fy, four
-fused multiply-adds in that order, frames in order), so its stack values and
-candidate lists must equal the direct-gather kernel's bit for bit.  Against
-the FP64 oracle the stated bar holds: |S - S64| <= 1e-5 max(|S64|, sqrt(N)).
+The register-window kernel forms each bilinear sample in factored form (the
+warp's horizontal interpolation shared by its 4 y-velocities, then two fused
+multiply-adds), the direct-gather kernel as four weighted taps; both are held
+to the stated bar against the FP64 oracle, |S - S64| <= 1e-5 max(|S64|,
+sqrt(N)), with exact coverage.  Candidate lists must equal the direct-gather
+kernel's exactly: the local-maximum resolver re-forms every reported value
+with one arithmetic, and the register-window pre-filter keeps a margin.
 Fields have ragged tiles, edge tiles, both signs of t - t_ref and fractional
-shifts; integer shifts reduce bilinear to nearest (Sec. 2.1 reading).
+shifts; integer shifts reduce bilinear to nearest bit for bit (Sec. 2.1
+reading).
 """
 import math
 
@@ -69,8 +72,9 @@ def test_bilinear_fast_dump_equals_generic_and_fp64(st, seed, shape):
             S, Cv = p.dump_stack(0, dev(fr), t, ks)
             p.candidates(dev(fr), t)
             assert p.last_stack_variant(0) == 1, "register-window kernel not used"
+        S = S.cpu().numpy().astype(np.float64)
         assert np.array_equal(Cv.cpu().numpy(), oC), tile
-        assert np.array_equal(S.cpu().numpy(), gS), tile
+        assert np.all(np.abs(S - oS) <= 1e-5 * np.maximum(np.abs(oS), math.sqrt(N))), tile
 
 
 @pytest.mark.parametrize("seed,shape,tau", [(25, dict(), 3.5),
@@ -130,7 +134,7 @@ def test_bilinear_fast_integer_shifts_equal_nearest(st):
         nS, nC = p.dump_stack(0, dev(fr), t, ks)
         ne = p.candidates(dev(fr), t)
     assert np.array_equal(bC.cpu().numpy(), nC.cpu().numpy())
-    # w00 = 1 and the other weights 0: fma(1, I, acc) + 0-products == acc + I
+    # fx = fy = 0: h = I exactly and fma(1, h, acc) then fma(0, ., acc) == acc + I
     assert np.array_equal(bS.cpu().numpy(), nS.cpu().numpy())
     assert bl.tobytes() == ne.tobytes()
 
@@ -146,7 +150,6 @@ def test_bilinear_fast_reduced_storage(st, storage):
         S, Cv = p.dump_stack(0, dev(fr), t, ks)
         got = p.candidates(dev(fr), t)
         assert p.last_stack_variant(0) == 1
-    assert np.array_equal(S.cpu().numpy(), gS.cpu().numpy())
     assert np.array_equal(Cv.cpu().numpy(), gC.cpu().numpy())
     assert got.tobytes() == gen.tobytes()
     # against FP64 on the rounded frames: FP32 accumulation error only
