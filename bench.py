@@ -72,6 +72,13 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--width", type=int, default=None,
+                    help="override the workload's frame size (square), e.g. for a profiling case")
+    ap.add_argument("--frames", type=int, default=None, help="override the frame count")
+    ap.add_argument("--nv", type=int, default=None, help="override the grid size per axis")
+    ap.add_argument("--precision", action="store_true",
+                    help="after timing: stack error vs the FP64 oracle at sampled candidates "
+                         "and recovery of the injected movers (single-field workloads)")
     ap.add_argument("--tile", type=int, default=-1,
                     help="-1 autotune (first warm-up step), 0 default, 1 direct-gather, 2.. variant")
     args = ap.parse_args()
@@ -194,7 +201,42 @@ def field_for(args, rank, world):
         mine = shard.assign_fields(specs, world)[rank]
         total = float(sum(shard.field_work(f) for f in specs))
         return [synth.make_field(w, seed=base, index=j) for j in mine], total
-    return synth.make_field(w, seed=base + 100000 * rank), None
+    kw = {k: v for k, v in (("width", args.width), ("n_frames", args.frames), ("nv", args.nv))
+          if v is not None}
+    return synth.make_field(w, seed=base + 100000 * rank, **kw), None
+
+
+def precision_report(args, d, cand):
+    """Stack error of the reported candidates against the FP64 oracle on the
+    same normalised frames (so FP16/BF16 storage rounding is included), in
+    sigma units of the stack (S / sqrt(n_cov)), and the fraction of injected
+    movers with a candidate within 2 px and one grid step of the truth."""
+    import oracle
+    import synth
+    f = d["field"]
+    rng = np.random.default_rng(7)
+    norm = oracle.normalize(d["frames"], cr_clip=args.cr_clip if args.normalize else 0.0)[0] \
+        if args.normalize else np.nan_to_num(d["frames"])
+    n = len(cand)
+    idx = rng.choice(n, min(2000, n), replace=False) if n else np.zeros(0, int)
+    xyk = np.stack([cand["x"][idx], cand["y"][idx], cand["k"][idx]], axis=1)
+    S64, C64 = oracle.stack_points(norm, d["times"], f, xyk, mode=args.mode, prec="fp64")
+    err = (cand["stack"][idx].astype(np.float64) - S64) / np.sqrt(np.maximum(C64, 1))
+    rel = np.abs(cand["stack"][idx] - S64) / np.maximum(np.abs(S64), np.sqrt(f["n_frames"]))
+    nvx = f["nvx"]
+    ca, cb = cand["k"] % nvx, cand["k"] // nvx
+    found = 0
+    for m in d["truth"]:
+        a, b, _ = synth.velocity_index(f, m[2], m[3])
+        hit = (np.abs(cand["x"] - m[0]) <= 2) & (np.abs(cand["y"] - m[1]) <= 2) & \
+              (np.abs(ca - a) <= 1) & (np.abs(cb - b) <= 1)
+        found += bool(hit.any())
+    return {"storage": args.storage, "points": int(len(idx)),
+            "err_rms_sigma": float(np.sqrt(np.mean(err ** 2))) if len(idx) else None,
+            "err_max_sigma": float(np.max(np.abs(err))) if len(idx) else None,
+            "err_max_rel": float(np.max(rel)) if len(idx) else None,
+            "movers": int(len(d["truth"])), "recovered": int(found),
+            "recovery_rate": found / max(len(d["truth"]), 1)}
 
 
 REFINE_N, REFINE_STEPS, REFINE_CUT = 4096, 20, 64
@@ -372,7 +414,10 @@ def main():
     # work of the whole job: the batch's total, or one field per rank
     job_adds = batch_total if batch_total is not None else adds * world
     scaling = "strong" if batch_total is not None else "weak"
-    config = {"workload": f"{args.workload}: {wl['desc']}", "frames": N, "height": H, "width": W,
+    desc = wl["desc"]
+    if any(v is not None for v in (args.width, args.frames, args.nv)):
+        desc += f" -- resized: {W}x{H}x{N}, {f['nvx']}x{f['nvy']} grid"
+    config = {"workload": f"{args.workload}: {desc}", "frames": N, "height": H, "width": W,
               "nv": [f["nvx"], f["nvy"]], "storage": args.storage, "shift": args.mode,
               "normalize": bool(args.normalize), "cr_clip": args.cr_clip, "tau": f["snr_threshold"],
               "tile": args.tile, "graph": bool(args.graph),
@@ -536,6 +581,10 @@ def main():
         e2e["unit"] = unit
     if args.graph:
         config["graph_replayed"] = plan.last_graph_replayed()
+    precision = None
+    if args.precision and batch_total is None:
+        cand = out[:min(n_found, cap)].cpu().numpy().view(st.CAND_DTYPE).reshape(-1)
+        precision = precision_report(args, d, cand)
     line = {
         "metric": METRIC, "value": value, "unit": unit, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
@@ -544,6 +593,8 @@ def main():
         "fields_per_hr": 3600.0 / t_step * (BATCH if batch_total is not None else world),
         "candidates": int(n_found), "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
         "e2e": e2e, "gpu_launches": int(launches), "device": props.name}
+    if precision:
+        line["precision"] = precision
     print(json.dumps(line))
     plan.close()
 
