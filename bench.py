@@ -34,6 +34,9 @@ WORKLOADS = {
                     "baselines 1-8 h, grid step 1 px/baseline, +-60 px/h, one plan"),
     "refine": dict(name="refine", desc="4096 candidates of a 2048x2048x300 field's 801x801 grid "
                    "search, 64x64 cutouts, 20 Adam steps"),
+    "front": dict(name="speculoos", desc="front end on the 2048x2048x256 field: median star "
+                  "removal over groups of 50 frames overlapping by 5, sums of every 13 frames, "
+                  "2x2 binning"),
 }
 METRIC = "G pixel*frame*velocity adds/s (2048x2048x256, 801x801 grid)"
 
@@ -399,6 +402,122 @@ def bench_refine(args, d, config, dev, world, rank, local):
     plan.close()
 
 
+FRONT_GROUP, FRONT_OVERLAP, FRONT_SUM = 50, 5, 13
+FRONT_METRIC = "front-end GB/s (median star removal + sums of 13 + 2x2 binning, 2048x2048x256)"
+
+
+def front_bytes(N, H, W, groups):
+    """Algorithmic bytes of one front-end pass: each kernel reads its input
+    once and writes its output once (FP32)."""
+    P = H * W
+    med = sum(2 * (e - s) * P * 4 for s, e in groups)
+    M = N // FRONT_SUM
+    sums = (M * FRONT_SUM + M) * P * 4
+    binb = N * P * 4 + N * (H // 2) * (W // 2) * 4
+    return med, sums, binb
+
+
+def front_reference(args, d, config):
+    """The front-end oracle (numpy) on a bounded crop of the same frames."""
+    from oracle import front
+    fr = d["frames"]
+    N = fr.shape[0]
+    c = 64
+    crop = np.ascontiguousarray(fr[:, :c, :c])
+    t0 = time.perf_counter()
+    front.median_subtract(crop[:FRONT_GROUP])
+    front.sum_frames(crop, d["times"], FRONT_SUM)
+    front.bin2x2(crop)
+    el = time.perf_counter() - t0
+    med, sums, binb = front_bytes(N, c, c, [(0, FRONT_GROUP)])
+    v = (med + sums + binb) / el / 1e9
+    sample = f"one group of {FRONT_GROUP} frames, sums and binning of a {c}x{c} crop, numpy oracle"
+    print(json.dumps({
+        "impl": "reference", "metric": FRONT_METRIC, "value": v, "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": config,
+        "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def bench_front(args, d, config, dev, world, rank, local):
+    """The pre-tracking front end on the headline cube: one step = median
+    removal over overlapping groups, the sums of every 13 frames and the
+    2x2-binned cube, each kernel timed with CUDA events on the stream."""
+    import torch
+    import paper_2303_07293_gb300 as st
+    from paper_2303_07293_gb300 import groups as grp
+    N, H, W = d["frames"].shape
+    stream = torch.cuda.current_stream(dev)
+    frames = torch.from_numpy(d["frames"]).to(dev)
+    out = torch.empty_like(frames)
+    gr = grp.group_ranges(N, FRONT_GROUP, FRONT_OVERLAP)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    def step():
+        ev[0].record(stream)
+        for s_, e_ in gr:
+            st.median_subtract(frames[s_:e_], out=out[s_:e_], stream=stream)
+        ev[1].record(stream)
+        sums, _ = st.sum_frames(frames, d["times"], FRONT_SUM, stream=stream)
+        ev[2].record(stream)
+        binned = st.bin2x2(frames, stream=stream)
+        ev[3].record(stream)
+        return sums, binned
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    tm = [0.0, 0.0, 0.0]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+        torch.cuda.synchronize()
+        for k in range(3):
+            tm[k] += ev[k].elapsed_time(ev[k + 1]) / 1e3
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_step = e0.elapsed_time(e1) / 1e3 / args.steps
+    med_b, sum_b, bin_b = front_bytes(N, H, W, gr)
+    total = med_b + sum_b + bin_b
+    if rank != 0:
+        return
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6780.0)
+    gbs = [b / (t / args.steps) / 1e9 for b, t in zip((med_b, sum_b, bin_b), tm)]
+    roof = {"bound": "hbm", "achieved": gbs[0], "peak": hbm, "unit": "GB/s",
+            "frac": gbs[0] / hbm, "traffic": None, "kernel": "k_median_subtract",
+            "launches_per_step": len(gr), "avg_launch_ms": tm[0] / args.steps / len(gr) * 1e3,
+            "peak_basis": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)",
+            "per_kernel_gbs": {"median_subtract": gbs[0], "sum_frames": gbs[1], "bin2x2": gbs[2]},
+            "per_kernel_frac": {"median_subtract": gbs[0] / hbm, "sum_frames": gbs[1] / hbm,
+                                "bin2x2": gbs[2] / hbm}}
+    cfg = dict(config, groups=[list(g) for g in gr], sum_every=FRONT_SUM)
+    cpu = None
+    if not args.no_cpu_baseline:
+        import io
+        import contextlib
+        buf = io.StringIO()
+        with contextlib.redirect_stdout(buf):
+            front_reference(args, d, config)
+        cpu = json.loads(buf.getvalue())["cpu_baseline"]
+    print(json.dumps({
+        "metric": FRONT_METRIC, "value": total / t_step / 1e9, "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+        "roofline": roof, "cpu_baseline": cpu, "clocks": clk, "e2e": None,
+        "gpu_launches": (len(gr) + 2) * args.steps,
+        "device": torch.cuda.get_device_properties(dev).name}))
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -433,6 +552,8 @@ def main():
             return
         if args.workload == "refine":
             return refine_reference(args, d, config)
+        if args.workload == "front":
+            return front_reference(args, d, config)
         unit = "G samples/s" if args.mode == "bilinear" else "G adds/s"
         rate, cores, sample, el = oracle_baseline(d, max(1.0, args.cpu_seconds / 3), args.mode)
         times = []
@@ -461,6 +582,8 @@ def main():
     import paper_2303_07293_gb300 as st
     if args.workload == "refine":
         return bench_refine(args, d, config, dev, world, rank, local)
+    if args.workload == "front":
+        return bench_front(args, d, config, dev, world, rank, local)
 
     frames = [torch.from_numpy(x["frames"]).to(dev) for x in ds]
     times = [x["times"] for x in ds]

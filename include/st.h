@@ -263,6 +263,34 @@ int32_t st_last_stack_variant(const st_plan_t* plan, int32_t field);
  * 0 otherwise. */
 int32_t st_last_graph_replayed(const st_plan_t* plan);
 
+/* ---- Pre-tracking front end (Sec. 2.1) --------------------------------
+ * Device FP32 cubes [N][H][W] row-major, caller-owned; the calls are
+ * asynchronous on cuda_stream (NULL: the legacy default stream) and allocate
+ * nothing.  Errors: ST_ERR_INVALID for NULL pointers, sizes <= 0 or (sums,
+ * binning) an output overlapping the input; ST_ERR_CUDA for a launch error. */
+
+/* Median star removal: d_out[i] = d_in[i] - m for every frame i, with m the
+ * per-pixel median over the N frames of the finite samples (NaN marks a
+ * masked sample; an even count takes (a + b) * 0.5 of the two middle values;
+ * a pixel with no finite sample gives NaN).  d_out may be d_in.  d_median
+ * [H][W] (may be NULL) receives m.  N <= 768, else ST_ERR_UNSUPPORTED. */
+st_status st_median_subtract(const float* d_in, int32_t n_frames, int32_t height,
+                             int32_t width, float* d_out, float* d_median, void* cuda_stream);
+
+/* Sums of every n_sum consecutive frames, in frame order with one FP32
+ * accumulator: M = floor(N / n_sum) frames into d_out [M][H][W] (a trailing
+ * partial group is dropped, so every sum has the same exposure).  h_times_out
+ * [M] (host, may be NULL) receives the FP64 mean of each group's h_times
+ * (h_times may be NULL when h_times_out is). */
+st_status st_sum_frames(const float* d_in, int32_t n_frames, int32_t height, int32_t width,
+                        int32_t n_sum, const double* h_times, float* d_out,
+                        double* h_times_out, void* cuda_stream);
+
+/* 2 x 2 binning: d_out [N][H/2][W/2] = ((p00 + p01) + p10) + p11 per block
+ * (flux kept); an odd last row or column is dropped. */
+st_status st_bin2x2(const float* d_in, int32_t n_frames, int32_t height, int32_t width,
+                    float* d_out, void* cuda_stream);
+
 /* FP32 add-rate microbenchmark (the roof of the nearest-shift stack): one
  * block of 1024 threads per SM, 16 independent add chains per thread, iters
  * iterations.  variant 0: scalar add.rn.f32; 1: paired add.rn.f32x2;

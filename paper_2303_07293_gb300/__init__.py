@@ -349,5 +349,61 @@ def search_noalloc(field, frames, times, capacity=1 << 16, mode="nearest", strea
     return out, cnt.value, status
 
 
+# ------------------------------------------------------ pre-tracking front end
+
+def _cube(frames):
+    import torch
+    if not (frames.is_cuda and frames.dtype == torch.float32 and frames.is_contiguous() and
+            frames.dim() == 3):
+        raise ValueError("frames must be a contiguous CUDA float32 tensor [N][H][W]")
+    return frames.shape
+
+
+def median_subtract(frames, out=None, with_median=False, stream=None):
+    """st_median_subtract: frames minus their per-pixel median over the frames
+    (finite samples; Sec. 2.1 star removal).  out may be frames (in place).
+    Returns out, or (out, median [H][W]) with with_median."""
+    import torch
+    N, H, W = _cube(frames)
+    out = torch.empty_like(frames) if out is None else out
+    med = torch.empty((H, W), dtype=torch.float32, device=frames.device) if with_median else None
+    L = lib()
+    L.st_median_subtract.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
+                                     C.c_void_p, C.c_void_p]
+    _check(L.st_median_subtract(_ptr(frames), N, H, W, _ptr(out),
+                                _ptr(med) if with_median else None, _stream_handle(stream)))
+    return (out, med) if with_median else out
+
+
+def sum_frames(frames, times, n_sum, stream=None):
+    """st_sum_frames: sums of every n_sum frames (a trailing partial group is
+    dropped) and the mean time stamp of each group."""
+    import torch
+    N, H, W = _cube(frames)
+    M = N // n_sum
+    out = torch.empty((max(M, 1), H, W), dtype=torch.float32, device=frames.device)
+    t = np.ascontiguousarray(times, np.float64)
+    tout = np.zeros(max(M, 1), np.float64)
+    L = lib()
+    L.st_sum_frames.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    _check(L.st_sum_frames(_ptr(frames), N, H, W, int(n_sum), _np_ptr(t), _ptr(out),
+                           _np_ptr(tout), _stream_handle(stream)))
+    return out[:M], tout[:M]
+
+
+def bin2x2(frames, stream=None):
+    """st_bin2x2: 2 x 2 block sums [N][H/2][W/2]."""
+    import torch
+    N, H, W = _cube(frames)
+    out = torch.empty((N, max(H // 2, 1), max(W // 2, 1)), dtype=torch.float32,
+                      device=frames.device)
+    L = lib()
+    L.st_bin2x2.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
+                            C.c_void_p]
+    _check(L.st_bin2x2(_ptr(frames), N, H, W, _ptr(out), _stream_handle(stream)))
+    return out[:, :H // 2, :W // 2]
+
+
 def version():
     return lib().st_version()

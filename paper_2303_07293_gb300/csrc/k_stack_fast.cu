@@ -55,25 +55,25 @@ namespace {
 constexpr int kXV = 8;           // x-velocities per block, one per warp (within a row group)
 constexpr int kMB = 4;           // y-velocities per block (staircase group)
 constexpr int kTX = 32;          // pixel tile width; its height is the variant's KY
-// Storage traits: TMA box width (elements; 16-byte rows), x alignment of the
-// box origin (16 bytes), and the largest column offset of a warp.
+// Storage traits: TMA box width (elements; 16-byte rows) and the largest
+// column offset of a warp (16-bit storage: the 4-bit packing's limit).
 template <typename T>
 struct Store;
 template <>
 struct Store<float> {
-  static constexpr int kBoxW = 40, kAlign = 4, kOColMax = 8;
+  static constexpr int kBoxW = 40;
   static constexpr CUtensorMapDataType kTma = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   __device__ static float f(float v) { return v; }
 };
 template <>
 struct Store<__half> {
-  static constexpr int kBoxW = 48, kAlign = 8, kOColMax = 15;
+  static constexpr int kBoxW = 48, kOColMax = 15;
   static constexpr CUtensorMapDataType kTma = CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
   __device__ static float f(__half v) { return __half2float(v); }
 };
 template <>
 struct Store<__nv_bfloat16> {
-  static constexpr int kBoxW = 48, kAlign = 8, kOColMax = 15;
+  static constexpr int kBoxW = 48, kOColMax = 15;
   static constexpr CUtensorMapDataType kTma = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   __device__ static float f(__nv_bfloat16 v) { return __bfloat162float(v); }
 };

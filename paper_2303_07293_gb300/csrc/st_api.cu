@@ -787,6 +787,64 @@ int64_t st_last_launch_count(const st_plan_t* p) { return p ? p->launches : 0; }
 
 int32_t st_last_graph_replayed(const st_plan_t* p) { return p && p->last_replayed ? 1 : 0; }
 
+static bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  const char* x = (const char*)a;
+  const char* y = (const char*)b;
+  return x < y + nb && y < x + na;
+}
+
+st_status st_median_subtract(const float* d_in, int32_t n_frames, int32_t height, int32_t width,
+                             float* d_out, float* d_median, void* cuda_stream) {
+  if (!d_in || !d_out) return fail(ST_ERR_INVALID, "NULL frames");
+  if (n_frames <= 0 || height <= 0 || width <= 0)
+    return fail(ST_ERR_INVALID, "n_frames, height and width must be > 0");
+  if (n_frames > median_max_frames())
+    return fail(ST_ERR_UNSUPPORTED, "median over at most %d frames (got %d)",
+                median_max_frames(), n_frames);
+  const int64_t P = (int64_t)height * width;
+  if (launch_median_subtract(d_in, n_frames, P, d_out, d_median, (cudaStream_t)cuda_stream) < 0)
+    return fail(ST_ERR_INVALID, "frame too large for the median kernel's grid");
+  CK(cudaGetLastError());
+  return ST_OK;
+}
+
+st_status st_sum_frames(const float* d_in, int32_t n_frames, int32_t height, int32_t width,
+                        int32_t n_sum, const double* h_times, float* d_out, double* h_times_out,
+                        void* cuda_stream) {
+  if (!d_in || !d_out) return fail(ST_ERR_INVALID, "NULL frames");
+  if (n_frames <= 0 || height <= 0 || width <= 0 || n_sum <= 0)
+    return fail(ST_ERR_INVALID, "n_frames, height, width and n_sum must be > 0");
+  if (h_times_out && !h_times) return fail(ST_ERR_INVALID, "h_times_out needs h_times");
+  const int64_t P = (int64_t)height * width;
+  const int M = n_frames / n_sum;
+  if (overlaps(d_in, sizeof(float) * P * n_frames, d_out, sizeof(float) * P * (M > 0 ? M : 0)))
+    return fail(ST_ERR_INVALID, "d_out overlaps d_in");
+  if (launch_sum_frames(d_in, n_sum, M, P, d_out, (cudaStream_t)cuda_stream) < 0)
+    return fail(ST_ERR_INVALID, "sizes exceed the sum kernel's grid");
+  CK(cudaGetLastError());
+  if (h_times_out)
+    for (int m = 0; m < M; ++m) {
+      double ts = 0.0;
+      for (int i = m * n_sum; i < (m + 1) * n_sum; ++i) ts += h_times[i];
+      h_times_out[m] = ts / n_sum;
+    }
+  return ST_OK;
+}
+
+st_status st_bin2x2(const float* d_in, int32_t n_frames, int32_t height, int32_t width,
+                    float* d_out, void* cuda_stream) {
+  if (!d_in || !d_out) return fail(ST_ERR_INVALID, "NULL frames");
+  if (n_frames <= 0 || height <= 0 || width <= 0)
+    return fail(ST_ERR_INVALID, "n_frames, height and width must be > 0");
+  const size_t nin = sizeof(float) * (size_t)n_frames * height * width;
+  const size_t nout = sizeof(float) * (size_t)n_frames * (height / 2) * (width / 2);
+  if (overlaps(d_in, nin, d_out, nout)) return fail(ST_ERR_INVALID, "d_out overlaps d_in");
+  if (launch_bin2x2(d_in, n_frames, height, width, d_out, (cudaStream_t)cuda_stream) < 0)
+    return fail(ST_ERR_INVALID, "sizes exceed the binning kernel's grid");
+  CK(cudaGetLastError());
+  return ST_OK;
+}
+
 int32_t st_last_stack_variant(const st_plan_t* p, int32_t field) {
   if (!p || field < 0 || field >= (int)p->F.size()) return -1;
   return p->F[field].last_variant;

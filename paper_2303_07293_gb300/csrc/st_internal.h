@@ -135,6 +135,16 @@ int launch_refine(const FieldDev* h_fds, int n_fields, const FieldDev* fds, CUte
                   float fwhm, float lr_pos, float lr_vel, float* J, float* snr, float* grad,
                   st_refined* out, int* err, cudaStream_t s);
 
+// Front end (Sec. 2.1): median star removal over a group of N frames (N <=
+// median_max_frames()), sums of every n_sum frames into M outputs, 2 x 2
+// binning.  Each returns the number of launches or -1 if the sizes exceed
+// the launch limits.
+int median_max_frames();
+int launch_median_subtract(const float* in, int N, int64_t P, float* out, float* median,
+                           cudaStream_t s);
+int launch_sum_frames(const float* in, int n_sum, int M, int64_t P, float* out, cudaStream_t s);
+int launch_bin2x2(const float* in, int N, int H, int W, float* out, cudaStream_t s);
+
 // Tiled TMA map of a field's cube [N][H][W] (storage type) with a box of
 // box_w x box_h x 1 elements, zero fill outside.  False if it cannot be built.
 bool encode_tile_map(CUtensorMap* map, const FieldDev& fd, int box_w, int box_h);
