@@ -79,6 +79,8 @@ def parse():
                     help="override the workload's frame size (square), e.g. for a profiling case")
     ap.add_argument("--frames", type=int, default=None, help="override the frame count")
     ap.add_argument("--nv", type=int, default=None, help="override the grid size per axis")
+    ap.add_argument("--tracks", action="store_true",
+                    help="after timing: link the candidates into tracks and time it")
     ap.add_argument("--precision", action="store_true",
                     help="after timing: stack error vs the FP64 oracle at sampled candidates "
                          "and recovery of the injected movers (single-field workloads)")
@@ -704,6 +706,17 @@ def main():
         e2e["unit"] = unit
     if args.graph:
         config["graph_replayed"] = plan.last_graph_replayed()
+    tracks = None
+    if args.tracks:
+        tt0 = torch.cuda.Event(enable_timing=True)
+        tt1 = torch.cuda.Event(enable_timing=True)
+        plan.link_tracks(out[:min(n_found, cap)], min(n_found, cap))   # warm-up
+        tt0.record(stream)
+        trk = plan.link_tracks(out[:min(n_found, cap)], min(n_found, cap))
+        tt1.record(stream)
+        torch.cuda.synchronize()
+        tracks = {"detections": int(min(n_found, cap)), "tracks": int(len(trk)),
+                  "link_ms": tt0.elapsed_time(tt1), "r_xy": 2, "r_v": 1}
     precision = None
     if args.precision and batch_total is None:
         cand = out[:min(n_found, cap)].cpu().numpy().view(st.CAND_DTYPE).reshape(-1)
@@ -718,6 +731,8 @@ def main():
         "e2e": e2e, "gpu_launches": int(launches), "device": props.name}
     if precision:
         line["precision"] = precision
+    if tracks:
+        line["tracks"] = tracks
     print(json.dumps(line))
     plan.close()
 

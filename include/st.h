@@ -108,6 +108,21 @@ typedef struct {
   int32_t n_cov;             /* frames covering the pixel */
 } st_candidate;
 
+/* One track: the linked detections of one object (Sec. 2.1 returns tracks
+ * with speed, PA, pixel coordinates and S/N), represented by its detection
+ * of highest S/N.  48 bytes. */
+typedef struct {
+  int32_t x, y;              /* pixel of the representative detection */
+  int32_t k;                 /* its velocity index */
+  int32_t field;
+  float stack, snr;          /* its stack value and S/N */
+  int32_t n_cov;             /* its coverage */
+  int32_t members;           /* detections linked into the track */
+  float vx, vy;              /* grid velocity of the representative, px per time unit */
+  float speed;               /* hypot(vx, vy) */
+  float pa;                  /* degrees in [0, 360), from -y towards -x (north up, east left) */
+} st_track;
+
 /* One refined detection: continuous motion and position at t_ref. */
 typedef struct {
   float vx, vy, x0, y0, flux;
@@ -262,6 +277,18 @@ int32_t st_last_stack_variant(const st_plan_t* plan, int32_t field);
  * given frame pointers and timestamps, replayed while they stay the same),
  * 0 otherwise. */
 int32_t st_last_graph_replayed(const st_plan_t* plan);
+
+/* Links the detections of the plan's last search into tracks: two
+ * detections of a field are linked when their pixels differ by at most r_xy
+ * in x and y and their velocity indices by at most r_v in a and b; a track
+ * is a connected component, reported with its detection of highest S/N
+ * (ties: the first in (field, k, y, x) order) and its size, tracks in the
+ * order of their first detection.  d_cand: device candidates [n] in the
+ * order st_stack_search returns them; d_tracks: device [capacity]; *h_count
+ * receives the number of tracks (ST_ERR_OVERFLOW if above capacity: the
+ * first capacity tracks are written).  Synchronises the plan's stream. */
+st_status st_link_tracks(st_plan_t* plan, const st_candidate* d_cand, int64_t n, int32_t r_xy,
+                         int32_t r_v, st_track* d_tracks, int64_t capacity, int64_t* h_count);
 
 /* ---- Pre-tracking front end (Sec. 2.1) --------------------------------
  * Device FP32 cubes [N][H][W] row-major, caller-owned; the calls are

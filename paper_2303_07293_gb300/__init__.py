@@ -24,6 +24,10 @@ MODE = {"nearest": 0, "bilinear": 1}
 
 CAND_DTYPE = np.dtype([("x", np.int32), ("y", np.int32), ("k", np.int32), ("field", np.int32),
                        ("stack", np.float32), ("snr", np.float32), ("n_cov", np.int32)])
+TRACK_DTYPE = np.dtype([("x", np.int32), ("y", np.int32), ("k", np.int32), ("field", np.int32),
+                        ("stack", np.float32), ("snr", np.float32), ("n_cov", np.int32),
+                        ("members", np.int32), ("vx", np.float32), ("vy", np.float32),
+                        ("speed", np.float32), ("pa", np.float32)])
 REFINED_DTYPE = np.dtype([("vx", np.float32), ("vy", np.float32), ("x0", np.float32),
                           ("y0", np.float32), ("flux", np.float32), ("snr", np.float32),
                           ("obj", np.float32), ("field", np.int32)])
@@ -251,6 +255,20 @@ class Plan:
                                _ptr(g) if grad else None))
         rec = out[:n].cpu().numpy().view(REFINED_DTYPE).reshape(-1)
         return (rec, g[:n]) if grad else rec
+
+    def link_tracks(self, cands, n=None, r_xy=2, r_v=1):
+        """st_link_tracks: the detections (device tensor [n, 7] int32 in the
+        order search returns them) linked into tracks; numpy TRACK_DTYPE."""
+        import torch
+        n = cands.shape[0] if n is None else n
+        L = lib()
+        L.st_link_tracks.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_int32,
+                                     C.c_void_p, C.c_int64, C.c_void_p]
+        out = torch.empty((max(n, 1), 12), dtype=torch.int32, device=cands.device)
+        cnt = C.c_int64()
+        _check(L.st_link_tracks(self._h, _ptr(cands), n, r_xy, r_v, _ptr(out), max(n, 1),
+                                C.byref(cnt)))
+        return out[:cnt.value].cpu().numpy().view(TRACK_DTYPE).reshape(-1)
 
     def refine_eval(self, theta, centre, field=None, fwhm=3.0, grad=True):
         """st_refine_eval: J [n], SNR [n] and (optionally) dJ/dtheta [n, 5] at

@@ -100,6 +100,8 @@ struct st_plan_s {
   double* d_tref = nullptr;    // per field
   double* d_grid = nullptr;    // per field: vx0, dvx, vy0, dvy
   CUtensorMap* d_maps = nullptr;  // per field: TMA map of the cube for the refinement
+  void* d_link_ws = nullptr;      // track-linking workspace
+  int64_t link_ws_bytes = 0;
   int* d_rerr = nullptr;          // refinement timeout flag
   double* d_sky = nullptr;
   st_candidate* d_hout = nullptr;
@@ -147,6 +149,7 @@ void free_plan(st_plan_t* p) {
   cudaFree(p->d_ctr);
   cudaFree(p->d_maps);
   cudaFree(p->d_rerr);
+  cudaFree(p->d_link_ws);
   if (p->h_ctr) cudaFreeHost(p->h_ctr);
   cudaFree(p->d_cand);
   cudaFree(p->d_keys);
@@ -786,6 +789,37 @@ st_status st_dump_stack(st_plan_t* p, int32_t field, const float* d_frames, cons
 int64_t st_last_launch_count(const st_plan_t* p) { return p ? p->launches : 0; }
 
 int32_t st_last_graph_replayed(const st_plan_t* p) { return p && p->last_replayed ? 1 : 0; }
+
+st_status st_link_tracks(st_plan_t* p, const st_candidate* d_cand, int64_t n, int32_t r_xy,
+                         int32_t r_v, st_track* d_tracks, int64_t capacity, int64_t* h_count) {
+  if (!p || !h_count) return fail(ST_ERR_INVALID, "NULL argument");
+  *h_count = 0;
+  if (n < 0 || (n > 0 && !d_cand) || capacity < 0 || (capacity > 0 && !d_tracks))
+    return fail(ST_ERR_INVALID, "n, capacity >= 0 and non-NULL buffers required");
+  if (r_xy < 0 || r_v < 0) return fail(ST_ERR_INVALID, "r_xy and r_v must be >= 0");
+  if (n > 0x7fffffffll) return fail(ST_ERR_UNSUPPORTED, "at most 2^31 - 1 detections");
+  if (!p->has_search) return fail(ST_ERR_INVALID, "st_link_tracks needs a prior st_stack_search");
+  if (n == 0) return ST_OK;
+  const int64_t need = link_workspace_bytes(n);
+  if (need > p->link_ws_bytes) {
+    cudaFree(p->d_link_ws);
+    p->d_link_ws = nullptr;
+    p->link_ws_bytes = 0;
+    CK(cudaMalloc(&p->d_link_ws, need));
+    p->link_ws_bytes = need;
+  }
+  int64_t nt = 0;
+  int l = launch_link_tracks(d_cand, n, p->d_fds, p->d_grid, r_xy, r_v, p->d_link_ws, d_tracks,
+                             capacity, &nt, p->s);
+  CK(cudaGetLastError());
+  if (l < 0) return fail(ST_ERR_CUDA, "track linking failed");
+  p->launches = l;
+  *h_count = nt;
+  if (nt > capacity)
+    return fail(ST_ERR_OVERFLOW, "%lld tracks exceed capacity %lld", (long long)nt,
+                (long long)capacity);
+  return ST_OK;
+}
 
 static bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
   const char* x = (const char*)a;

@@ -135,6 +135,14 @@ int launch_refine(const FieldDev* h_fds, int n_fields, const FieldDev* fds, CUte
                   float fwhm, float lr_pos, float lr_vel, float* J, float* snr, float* grad,
                   st_refined* out, int* err, cudaStream_t s);
 
+// Tracks: links the sorted candidates [n] into components (workspace of
+// link_workspace_bytes(n) bytes); writes up to cap tracks, *n_tracks = all.
+// Synchronises s.  Returns launches or -1.
+int64_t link_workspace_bytes(int64_t n);
+int launch_link_tracks(const st_candidate* c, int64_t n, const FieldDev* fds, const double* grid,
+                       int r_xy, int r_v, void* ws, st_track* out, int64_t cap,
+                       int64_t* n_tracks, cudaStream_t s);
+
 // Front end (Sec. 2.1): median star removal over a group of N frames (N <=
 // median_max_frames()), sums of every n_sum frames into M outputs, 2 x 2
 // binning.  Each returns the number of launches or -1 if the sizes exceed
