@@ -34,6 +34,8 @@ WORKLOADS = {
                     "baselines 1-8 h, grid step 1 px/baseline, +-60 px/h, one plan"),
     "refine": dict(name="refine", desc="4096 candidates of a 2048x2048x300 field's 801x801 grid "
                    "search, 64x64 cutouts, 20 Adam steps"),
+    "multinight": dict(name="multinight", desc="2 nights x 64 frames of 1024x1024 (2 min cadence, "
+                       "24 h apart), grid +-5 px/h at 1 px over the baseline (243x243)"),
     "front": dict(name="speculoos", desc="front end on the 2048x2048x256 field: median star "
                   "removal over groups of 50 frames overlapping by 5, sums of every 13 frames, "
                   "2x2 binning"),
@@ -199,7 +201,8 @@ def field_for(args, rank, world):
     field of its own (weak scaling)."""
     import synth
     w = WORKLOADS[args.workload]["name"]
-    base = synth.BASE_SEED + {"tiny": 1, "mid": 2, "speculoos": 3, "batched": 4, "refine": 5}[w]
+    base = synth.BASE_SEED + {"tiny": 1, "mid": 2, "speculoos": 3, "batched": 4, "refine": 5,
+                              "multinight": 6}[w]
     if w == "batched":
         from paper_2303_07293_gb300 import shard
         specs = [synth.batched_field(base, j) for j in range(BATCH)]

@@ -327,6 +327,13 @@ st_status st_bin2x2(const float* d_in, int32_t n_frames, int32_t height, int32_t
 st_status st_probe_add_rate(int32_t variant, int32_t iters, double* adds_per_clk_per_sm,
                             double* tadds_per_s);
 
+/* Failure-detection probe: one thread waits, with the bounded wait every
+ * pipeline of the library uses, on an mbarrier phase that nothing completes,
+ * and gives up after limit_us microseconds (1 .. 2 000 000).  *h_timed_out
+ * receives 1 when the wait ran out (the expected outcome), *h_waited_us the
+ * time the kernel measured.  The context stays usable afterwards. */
+st_status st_probe_wait_timeout(int32_t limit_us, int32_t* h_timed_out, double* h_waited_us);
+
 #ifdef __cplusplus
 }
 #endif

@@ -344,6 +344,17 @@ def probe_add_rate(variant=1, iters=20000):
     return a.value, t.value
 
 
+def probe_wait_timeout(limit_us=100000):
+    """st_probe_wait_timeout: (timed out?, microseconds waited) of a bounded
+    wait on a phase that never completes."""
+    L = lib()
+    L.st_probe_wait_timeout.argtypes = [C.c_int32, C.c_void_p, C.c_void_p]
+    flag = C.c_int32()
+    us = C.c_double()
+    _check(L.st_probe_wait_timeout(int(limit_us), C.byref(flag), C.byref(us)))
+    return bool(flag.value), us.value
+
+
 def search_noalloc(field, frames, times, capacity=1 << 16, mode="nearest", stream=None):
     """st_stack_search_noalloc: one-field search whose scratch lives in a fixed
     device array inside the library (for callers that cannot allocate device

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "st_internal.h"
+#include "st_tma.cuh"
 
 namespace st {
 
@@ -107,5 +108,50 @@ extern "C" st_status st_probe_add_rate(int32_t variant, int32_t iters, double* a
   double adds_per_block = 1024.0 * 16.0 * iters;
   *adds_per_clk_per_sm = adds_per_block / (double)h_cyc[sms / 2];
   *tadds_per_s = adds_per_block * sms / (ms * 1e-3) / 1e12;
+  return ST_OK;
+}
+
+namespace st {
+namespace {
+
+// Waits on the first phase of an mbarrier that expects one arrival which
+// never comes; the wait is bounded by limit_ns of the global timer.
+__global__ void k_wait_probe(uint64_t limit_ns, int* timed_out, unsigned long long* waited_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  mbar_init_fence();
+  const uint64_t t0 = global_ns();
+  const bool ok = mbar_wait(&bar, 0u, limit_ns);
+  *waited_ns = global_ns() - t0;
+  *timed_out = ok ? 0 : 1;
+}
+
+}  // namespace
+}  // namespace st
+
+extern "C" st_status st_probe_wait_timeout(int32_t limit_us, int32_t* h_timed_out,
+                                           double* h_waited_us) {
+  using namespace st;
+  if (!h_timed_out || !h_waited_us) return ST_ERR_INVALID;
+  if (limit_us < 1 || limit_us > 2000000) return ST_ERR_INVALID;
+  int* d_flag = nullptr;
+  unsigned long long* d_ns = nullptr;
+  if (cudaMalloc(&d_flag, sizeof(int)) != cudaSuccess) return ST_ERR_OOM;
+  if (cudaMalloc(&d_ns, sizeof(unsigned long long)) != cudaSuccess) {
+    cudaFree(d_flag);
+    return ST_ERR_OOM;
+  }
+  k_wait_probe<<<1, 32>>>((uint64_t)limit_us * 1000ull, d_flag, d_ns);
+  cudaError_t e = cudaDeviceSynchronize();
+  int flag = 0;
+  unsigned long long ns = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&ns, d_ns, sizeof(ns), cudaMemcpyDeviceToHost);
+  cudaFree(d_flag);
+  cudaFree(d_ns);
+  if (e != cudaSuccess) return ST_ERR_CUDA;
+  *h_timed_out = flag;
+  *h_waited_us = ns / 1000.0;
   return ST_OK;
 }

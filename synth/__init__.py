@@ -16,6 +16,9 @@ frames at 0.35"/px, Sec. 3), which is not available:
 * ``batched``   24 fields: N in [40, 400], sizes {512, 1024, 2048}^2, baselines
                 1-8 h, grid step 1 px over the baseline, +-60 px/h
 * ``refine``    ``speculoos`` with 300 frames (the refinement workload)
+* ``multinight`` 2 nights x 64 frames of 1024^2 (2 min cadence, nights 24 h
+                apart), slow movers (<= 5 px/h), grid +-5 px/h with a step of
+                1 px over the whole baseline (a large, sparse-in-time grid)
 """
 import ctypes as C
 import math
@@ -128,7 +131,7 @@ def make_field(name, seed=None, **kw):
     nv (grid size per axis, keeping the step), tau."""
     if seed is None:
         seed = BASE_SEED + {"tiny": 1, "mid": 2, "speculoos": 3, "batched": 4,
-                            "refine": 5}.get(name, 0)
+                            "refine": 5, "multinight": 6}.get(name, 0)
     rng = np.random.Generator(np.random.Philox(seed))
     fwhm = 3.0
     if name == "tiny":
@@ -182,6 +185,27 @@ def make_field(name, seed=None, **kw):
         render_movers(frames, t, t_ref, truth, fwhm)
         return dict(field=f, frames=frames, times=t, truth=truth, unit="h", fwhm=fwhm,
                     n_cosmics=int(hits))
+    if name == "multinight":
+        W = H = kw.get("width", 1024)
+        nights = kw.get("nights", 2)
+        per = kw.get("n_frames", 128) // nights
+        N = per * nights
+        night = np.arange(per) * (2.0 / 60.0)            # 2 min cadence, hours
+        t = np.concatenate([night + 24.0 * j for j in range(nights)])
+        t_ref = float(0.5 * (t[0] + t[-1]))              # mid-baseline: |dt| <= baseline / 2
+        vmax = kw.get("vmax", 5.0)
+        base = float(t[-1] - t[0])
+        dv = 1.0 / base                                   # 1 px over the whole baseline
+        nv = kw.get("nv", 2 * int(math.floor(vmax / dv)) + 1)
+        f = field_params(W, H, N, t_ref, -dv * (nv // 2), dv, nv, -dv * (nv // 2), dv, nv,
+                         kw.get("tau", 5.0))
+        frames = noise(N, H, W, seed)
+        m = int(kw.get("n_movers", 10))
+        truth = _place_movers(rng, m, W, H, t, t_ref, lambda r: r.uniform(0.0, vmax),
+                              lambda r: r.uniform(0.3, 1.0), 2 * fwhm) if m else \
+            np.zeros((0, 5))
+        render_movers(frames, t, t_ref, truth, fwhm)
+        return dict(field=f, frames=frames, times=t, truth=truth, unit="h", fwhm=fwhm)
     if name == "batched":
         j = kw.get("index", 0)
         rng, f, t, B = _batched_params(seed, j, kw)

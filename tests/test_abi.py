@@ -56,3 +56,28 @@ def test_invalid_arguments_are_rejected_without_gpu_work():
     assert L.st_plan(C.byref(good), 0, C.byref(opts), None, C.byref(h)) == st.ST_ERR_INVALID
     assert L.st_stack_search(None, None, None, None, 0, None) == st.ST_ERR_INVALID
     L.st_free(None)  # NULL-safe
+
+
+def test_new_entry_points_validate_arguments_without_gpu_work():
+    import paper_2303_07293_gb300 as st
+    L = st.lib()
+    P = C.c_void_p
+    L.st_median_subtract.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, P, P, P]
+    L.st_sum_frames.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P, P, P, P]
+    L.st_bin2x2.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, P, P]
+    L.st_link_tracks.argtypes = [P, P, C.c_int64, C.c_int32, C.c_int32, P, C.c_int64, P]
+    L.st_probe_wait_timeout.argtypes = [C.c_int32, P, P]
+    fake = P(0x1000)
+    assert L.st_median_subtract(None, 4, 4, 4, fake, None, None) == st.ST_ERR_INVALID
+    assert L.st_median_subtract(fake, 0, 4, 4, fake, None, None) == st.ST_ERR_INVALID
+    assert L.st_median_subtract(fake, 769, 4, 4, fake, None, None) == st.ST_ERR_UNSUPPORTED
+    assert L.st_sum_frames(fake, 8, 4, 4, 0, None, P(0x90000), None, None) == st.ST_ERR_INVALID
+    # output inside the input cube
+    assert L.st_sum_frames(fake, 8, 4, 4, 2, None, P(0x1010), None, None) == st.ST_ERR_INVALID
+    assert L.st_bin2x2(fake, 2, 8, 8, P(0x1020), None) == st.ST_ERR_INVALID
+    cnt = C.c_int64()
+    assert L.st_link_tracks(None, fake, 1, 2, 1, fake, 1, C.byref(cnt)) == st.ST_ERR_INVALID
+    f = C.c_int32()
+    d = C.c_double()
+    assert L.st_probe_wait_timeout(0, C.byref(f), C.byref(d)) == st.ST_ERR_INVALID
+    assert L.st_probe_wait_timeout(3000000, C.byref(f), C.byref(d)) == st.ST_ERR_INVALID
