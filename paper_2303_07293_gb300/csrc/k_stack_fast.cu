@@ -1,37 +1,45 @@
 // k_stack_fast.cu — register-window shift-and-stack kernel for sm_103a.
 //
-// Computes the same stack as the generic kernel (Sec. 1 / Sec. 2.1: every
-// frame shifted by the trial motion v*(t_i - t_ref) and summed in frame
-// order with one FP32 accumulator per output), laid out for the GB300 FP32
-// pipe, for nearest-pixel and bilinear sampling:
+// Computes the stack of the generic kernel (Sec. 1 / Sec. 2.1: every frame
+// shifted by the trial motion v*(t_i - t_ref) and summed in frame order with
+// one FP32 accumulator per output), laid out for the GB300 FP32 pipe, for
+// nearest-pixel and bilinear sampling, over every field of a plan in one
+// persistent launch:
 //
-// * A block owns a 32 x KY pixel tile and a velocity tile of 8 x-velocities
-//   (one per consumer warp) times 4 y-velocities (shared by all warps).  Lane
-//   l owns column X0 + l; each thread accumulates the KY rows of its column
-//   for its warp's x-velocity and the 4 y-velocities.
-// * Per frame, a producer warp issues a TMA tile load of the block's
-//   footprint (zero-filled outside the frame) into a ring of shared-memory
-//   stages guarded by mbarriers (full: bytes landed; empty: all warps done).
-//   Every wait is bounded.
+// * A work item is a 32 x KY pixel tile (64 x KY for the column-pair
+//   variant) of one field times a velocity tile of 8 x-velocities (one per
+//   consumer warp) and 4 y-velocities (shared by all warps).  Lane l owns
+//   column X0 + l (and X0 + 32 + l); each thread accumulates the KY rows of
+//   its column for its warp's x-velocity and the 4 y-velocities.
+// * A producer warp takes items from a work counter (fields longest first),
+//   publishes each item in a shared-memory slot ring, and per frame issues a
+//   TMA tile load of the item's footprint (zero-filled outside the frame)
+//   into a ring of shared-memory stages guarded by mbarriers (full: bytes
+//   landed; empty: all warps done), staging the frame's column offsets,
+//   staircase pattern id (and bilinear fractions) beside it.  Every wait is
+//   bounded.
 // * A warp's x-shift is only an address: lane l reads column l + o_w, so the
 //   32 lanes read 32 consecutive words (no bank conflicts, any alignment).
 // * Each thread loads a window of its column (KY + 3 rows; bilinear: KY + 4
 //   rows of the column and its right neighbour) and reuses every value for
 //   the 4 y-velocities: y-velocity j reads window row r + c_j for output row
 //   r.  The row offsets c_j form a monotone staircase with steps of 0 or 1
-//   (15 patterns); the pattern is the same for the whole block in a frame and
-//   comes from the kernel parameters, so one uniform switch per frame picks a
-//   straight-line body.  Nearest: even offsets use paired adds (add.f32x2) on
-//   row pairs, odd offsets scalar adds.  Bilinear: four fused multiply-adds
-//   per sample with the weights of the warp's x-fraction and the y-velocity's
-//   y-fraction, in the generic kernel's order.
-// * After the last frame, outputs are compared with the block's lowest
+//   (15 patterns); the pattern is the same for the whole block in a frame, so
+//   one switch per frame picks a straight-line body.  Nearest: even offsets
+//   use paired adds (add.f32x2) on row pairs, odd offsets scalar adds (the
+//   column-pair variant pairs the two columns instead, so every add is
+//   paired).  Bilinear: the warp's horizontal interpolation of each window
+//   row is formed once and shared by the 4 y-velocities, each adding
+//   (1 - fy) h[r + c_j] + fy h[r + c_j + 1] as two fused multiply-adds.
+// * After the last frame, outputs are compared with the item's lowest
 //   possible threshold; the rare survivors go to the warp-aggregated pending
-//   list, where the resolver forms their exact coverage and local maximum.
+//   list, where the resolver forms their exact value, coverage and local
+//   maximum with the generic kernel's arithmetic.
 //
-// The sums are the same FP32 operations in the same order as the generic
-// kernel (out-of-frame taps read +0.0 from the TMA zero fill, as the generic
-// kernel's taps do), so the two kernels agree bit for bit.
+// Nearest sums are the same FP32 additions in the same order as the generic
+// kernel (out-of-frame samples read +0.0 from the TMA zero fill), so the two
+// kernels agree bit for bit; bilinear sums agree to FP32 rounding (the
+// pre-filter keeps a margin for it).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
