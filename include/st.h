@@ -88,11 +88,20 @@ typedef struct {
                                 I = (R - mu)/sigma, NaN -> 0; 0: frames are used
                                 as given (NaN propagates) */
   float cr_clip;             /* with normalize: zero |I| > cr_clip; 0 disables */
-  int32_t use_graph;         /* 1: capture the search of all fields into a CUDA
-                                graph on the first call and replay it later */
-  int32_t tile;              /* stack kernel: -1 = autotuned register-window variant,
-                                0 = default, 1 = direct-gather kernel only,
-                                2.. = register-window variant (tile - 2) */
+  int32_t use_graph;         /* 1: the device part of a search (normalisation,
+                                the stack launch, local maxima, counters) is
+                                captured into a CUDA graph on the first call
+                                with given frame pointers and timestamps and
+                                replayed while both stay the same (shift tables
+                                are rebuilt only when the timestamps change) */
+  int32_t tile;              /* stack kernel: -1 = register-window variant chosen
+                                by timing the variants on the field with the most
+                                work (cached in tune_cache), 0 = default variant,
+                                1 = direct-gather kernel only, 2.. = register-
+                                window variant (tile - 2) of the list for the
+                                storage type and sampling (out of range: 0); a
+                                field whose motion does not fit the window takes
+                                the direct-gather kernel */
   const char* tune_cache;    /* JSON file for autotuned tiles, or NULL */
   int64_t pending_capacity;  /* above-threshold points held before the local-max
                                 test; 0 selects a default of 4 Mi points */
@@ -163,7 +172,11 @@ void st_free(st_plan_t* plan);
  * when the total exceeds capacity: the first `capacity` records of the sorted
  * list are written and *h_count holds the total, so a retry with a larger
  * buffer succeeds.  Returns ST_ERR_OVERFLOW with *h_count = -1 when the
- * above-threshold points exceed the plan's pending_capacity. */
+ * above-threshold points exceed the plan's pending_capacity, and
+ * ST_ERR_TIMEOUT (*h_count = -1) when a pipeline wait of the stack kernel
+ * gave up after 2 s (the device stays usable).  Every field whose motion fits
+ * the register-window kernel is searched in one persistent launch; shift
+ * tables are rebuilt only when a field's timestamps change. */
 st_status st_stack_search(st_plan_t* plan, const float* const* d_frames,
                           const double* const* h_times, st_candidate* d_out,
                           int64_t capacity, int64_t* h_count);
