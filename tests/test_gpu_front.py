@@ -38,6 +38,7 @@ def cube(seed, N, H, W, nan_frac=0.02, dup=False):
 
 
 @pytest.mark.parametrize("N,H,W,dup", [(1, 5, 7, False), (2, 9, 33, False), (7, 37, 53, False),
+                                       (32, 11, 13, True), (33, 17, 19, False),
                                        (50, 64, 96, False), (64, 31, 40, True),
                                        (257, 16, 24, False), (768, 4, 40, False)])
 def test_median_subtract_bitexact(st, N, H, W, dup):
