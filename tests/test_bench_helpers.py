@@ -1,0 +1,42 @@
+"""Host-side helpers of bench.py (no GPU): the algorithmic-work formulas the
+bench lines divide by, the code hash that keeps a stored DRAM traffic figure
+tied to the kernel it was measured on, and the precision / recovery report
+(fed here with the oracle's own candidates, which must score exactly)."""
+import argparse
+
+import numpy as np
+
+import bench
+import oracle
+import synth
+
+
+def test_work_formulas():
+    # refinement: candidates x cutout pixels x frames x (steps + 1) evaluations
+    assert bench.refine_units(300) == 4096 * 64 * 64 * 300 * 21
+    # front end: each kernel reads its input once and writes its output once
+    med, sums, binb = bench.front_bytes(256, 2048, 2048, [(0, 50), (45, 95)])
+    P = 2048 * 2048
+    assert med == 2 * (50 + 50) * P * 4
+    assert sums == (19 * 13 + 19) * P * 4            # 19 sums of 13 frames
+    assert binb == 256 * P * 4 + 256 * 1024 * 1024 * 4
+
+
+def test_code_hash_ignores_comments_only():
+    h = bench.stack_source_sha()
+    assert len(h) == 12 and h == bench.stack_source_sha()
+
+
+def test_precision_report_on_oracle_candidates():
+    from paper_2303_07293_gb300 import CAND_DTYPE
+    d = synth.make_field("tiny", seed=synth.BASE_SEED + 1)
+    r = oracle.search(np.nan_to_num(d["frames"]), d["times"], d["field"], prec="fp32")
+    c = np.zeros(len(r), CAND_DTYPE)
+    for k in ("x", "y", "k", "n_cov"):
+        c[k] = r[k]
+    c["stack"] = r["stack"]
+    c["snr"] = r["snr"]
+    args = argparse.Namespace(normalize=0, cr_clip=0.0, mode="nearest", storage="f32")
+    rep = bench.precision_report(args, d, c)
+    assert rep["points"] == len(c) and rep["err_max_rel"] < 1e-6
+    assert rep["recovered"] == rep["movers"] == 3
