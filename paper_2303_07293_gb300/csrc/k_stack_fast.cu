@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
   extern __shared__ __align__(128) float smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[S];
   __shared__ __align__(8) uint64_t empty_bar[S];
-  __shared__ uint32_t slot_ocol[S * F];     // packed 4-bit column offsets of the 8 warps
+  __shared__ __align__(16) uint32_t slot_ocol[S * F];  // packed 4-bit column offsets of the 8 warps
   __shared__ uint32_t slot_ids[S];          // packed 8-bit pattern ids of the stage's frames
   __shared__ float slot_fx[BL ? S * F * kXV : 1];  // bilinear: x-fraction of each warp
   __shared__ float4 slot_fy[BL ? S * F : 1];       // bilinear: y-fractions of the 4 y-velocities
@@ -545,13 +545,22 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
       }
       const uint32_t idw = slot_ids[c_slot];  // the stage's pattern ids
       const T* stage = smem + (size_t)(c_slot * F) * box_floats + lane;
-      uint32_t oc_next = slot_ocol[c_slot * F];
+      // this warp's column offsets of the stage's frames, 4 bits each, from
+      // one vector load of the stage's packed words
+      uint32_t ocw = 0;
+      if constexpr (F == 4) {
+        const uint4 q = *reinterpret_cast<const uint4*>(slot_ocol + c_slot * F);
+        ocw = ((q.x >> (4 * xw)) & 15u) | (((q.y >> (4 * xw)) & 15u) << 4) |
+              (((q.z >> (4 * xw)) & 15u) << 8) | (((q.w >> (4 * xw)) & 15u) << 12);
+      } else {
+#pragma unroll
+        for (int fi = 0; fi < F; ++fi)
+          ocw |= ((slot_ocol[c_slot * F + fi] >> (4 * xw)) & 15u) << (4 * fi);
+      }
 #pragma unroll 1
       for (int fi = 0; fi < F; ++fi) {
         const int id = (idw >> (8 * fi)) & 0xffu;
-        const uint32_t oc = oc_next;
-        if (fi + 1 < F) oc_next = slot_ocol[c_slot * F + fi + 1];
-        const T* col = stage + fi * box_floats + ((oc >> (4 * xw)) & 15u);
+        const T* col = stage + fi * box_floats + ((ocw >> (4 * fi)) & 15u);
         if constexpr (BL) {
           float h[KY + 4];
           const float fxw = slot_fx[(c_slot * F + fi) * kXV + xw];
