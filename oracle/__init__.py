@@ -135,6 +135,49 @@ def stack_points(frames, t, field, xyk, mode="nearest", prec="fp64"):
     return S, Cv
 
 
+def candidates_at(frames, t, field, xyk, mode="nearest", prec="fp32"):
+    """The detection rule of Sec. 2.1 evaluated point by point, for fields too
+    large to search whole: for each (x, y, k) row of xyk, whether it is a
+    candidate (coverage n_cov >= n_min, S >= fl32(tau sqrt(n_cov)), and a
+    local maximum of S_k over the in-frame neighbours with n_cov >= n_min:
+    strictly above earlier neighbours in raster order, at least equal to
+    later ones), with its S, n_cov and S/N.  The same rule as ``search``,
+    with S and n_cov of the point and its 8 neighbours from ``stack_points``.
+    Returns (is_cand bool [n], S float64 [n], n_cov int32 [n], snr float64 [n])."""
+    xyk = np.ascontiguousarray(xyk, dtype=np.int64).reshape(-1, 3)
+    W, H, N = int(field["width"]), int(field["height"]), int(field["n_frames"])
+    nmin = int(field.get("min_coverage", 0)) or (N + 1) // 2
+    tau = np.float32(field["snr_threshold"])
+    n = len(xyk)
+    offs = [(dx, dy) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]   # raster order; centre j = 4
+    pts = np.repeat(xyk, 9, axis=0)
+    pts[:, 0] += np.tile([dx for dx, _ in offs], n)
+    pts[:, 1] += np.tile([dy for _, dy in offs], n)
+    inside = (pts[:, 0] >= 0) & (pts[:, 0] < W) & (pts[:, 1] >= 0) & (pts[:, 1] < H)
+    S = np.zeros(len(pts))
+    Cv = np.zeros(len(pts), np.int32)
+    if inside.any():
+        S[inside], Cv[inside] = stack_points(frames, t, field, pts[inside], mode, prec)
+    S, Cv, inside = S.reshape(n, 9), Cv.reshape(n, 9), inside.reshape(n, 9)
+    s, c = S[:, 4], Cv[:, 4]
+    th = (np.float64(tau) * np.sqrt(c.astype(np.float64))).astype(np.float32)
+    if prec == "fp32":
+        above = s.astype(np.float32) >= th
+        rsq = np.where(c > 0, 1.0 / np.sqrt(np.maximum(c, 1).astype(np.float64)), 0.0)
+        snr = (s.astype(np.float32) * rsq.astype(np.float32)).astype(np.float64)
+    else:
+        above = s >= th.astype(np.float64)
+        snr = s / np.sqrt(np.maximum(c, 1).astype(np.float64))
+    ok = inside[:, 4] & (c >= nmin) & above
+    for j in range(9):
+        if j == 4:
+            continue
+        live = inside[:, j] & (Cv[:, j] >= nmin)
+        beats = s > S[:, j] if j < 4 else s >= S[:, j]
+        ok &= beats | ~live
+    return ok, s, c, snr
+
+
 def search(frames, t, field, mode="nearest", prec="fp32", k_begin=0, k_end=None, cap=None):
     """Sorted candidates as a structured numpy array (x, y, k, n_cov, stack, snr)."""
     frames = _f32(frames)
