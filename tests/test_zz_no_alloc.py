@@ -4,9 +4,10 @@ Callers that cannot allocate device memory when they search (inside a CUDA
 stream capture, or with device memory reserved up front by another allocator)
 use this entry point; its scratch is a fixed array inside the library.  It
 must give the same sorted candidates as the planned search, on consecutive
-calls that reuse the array.  This file is named to be collected last, so a
-run that stops at the first failure has run every other test first; it also
-passes alone in a fresh process.
+calls that reuse the array.  This file is named to be collected after the
+other tests (only the long full-size parity test follows it), so a run that
+stops at the first failure has run them first; it also passes alone in a
+fresh process.
 """
 import ctypes as C
 

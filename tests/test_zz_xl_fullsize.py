@@ -1,0 +1,185 @@
+"""Parity at the headline size: one 2048^2 field of 256 frames (50 s cadence,
+cosmic rays, 100 movers) and the 801 x 801 velocity grid (+-100 px/h, step
+0.25 px/h), searched with the options the benchmark times: FP32 storage,
+nearest shifts, the autotuned register-window variant in one persistent
+launch.
+
+The oracle cannot search all 641 601 velocity planes inside a test, so it
+checks what it can compute at this size, against the bars of the small-size
+parity tests (readings of Sec. 2.1 of Burdanov, Hasler & de Wit 2023):
+
+* whole planes: the GPU's candidates in runs of four consecutive velocity
+  planes (through three injected movers, the grid's first and last planes,
+  where coverage is partial over much of the field, and two random runs)
+  equal the oracle's list for those planes bit for bit;
+* sampled candidates: 2000 reported candidates re-evaluated point by point
+  by the oracle's rule (``oracle.candidates_at``): each is a candidate, with
+  the same stack, coverage and S/N bit for bit;
+* mover windows: around every injected mover (+-2 px, +-1 grid step in each
+  velocity axis) the GPU's candidates equal the oracle's, point by point;
+* normalisation of the raw cube: sigma within 1e-12 relative, mu within
+  1e-12 sigma (the noise frames have no sky level, so mu is near zero), and
+  every output within 1 ulp of the oracle's or 1e-12 in sigma units (an
+  output where the raw value and mu nearly cancel is set by the last bits
+  of the FP64 mean).
+
+The oracle normalises the raw frames (with the cosmic-ray clip at 10 sigma)
+and the GPU search runs on that cube, so both sides stack the same input.
+The file is named to be collected last: it takes about two minutes.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+torch = pytest.importorskip("torch")
+
+CR_CLIP = 10.0
+RUN = 4          # planes per run
+N_POINTS = 2000  # sampled candidates
+
+
+@pytest.fixture(scope="module")
+def st():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2303_07293_gb300 as m
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return m
+
+
+@pytest.fixture(scope="module")
+def field():
+    d = synth.make_field("speculoos")
+    cube, mu, sd = oracle.normalize(d["frames"], cr_clip=CR_CLIP)
+    return d, cube, mu, sd
+
+
+@pytest.fixture(scope="module")
+def found(st, field):
+    d, cube, _, _ = field
+    frames = torch.from_numpy(cube).cuda()
+    with st.Plan(d["field"], storage="f32", mode="nearest", tile=-1,
+                 pending_capacity=1 << 24) as p:
+        got = p.candidates(frames, d["times"], capacity=1 << 22)
+        used = p.last_stack_variant(0)
+    del frames
+    torch.cuda.empty_cache()
+    return got, used
+
+
+def _key(x, y, k):
+    return (np.asarray(k, np.int64) << 30) | (np.asarray(y, np.int64) << 15) | \
+        np.asarray(x, np.int64)
+
+
+def plane_runs(d, seed=11):
+    """Starts of the runs of RUN consecutive velocity planes checked whole."""
+    f = d["field"]
+    nk = f["nvx"] * f["nvy"]
+    starts = [0, nk - RUN]
+    for m in d["truth"][:3]:
+        _, _, k = synth.velocity_index(f, m[2], m[3])
+        starts.append(int(min(max(k - 1, 0), nk - RUN)))
+    rng = np.random.default_rng(seed)
+    starts += [int(s) for s in rng.integers(0, nk - RUN, size=2)]
+    return sorted(set(starts))
+
+
+def check_planes(got, cube, d, starts):
+    """The GPU's candidates in each run of planes equal the oracle's."""
+    total = 0
+    for k0 in starts:
+        ref = oracle.search(cube, d["times"], d["field"], prec="fp32", k_begin=k0,
+                            k_end=k0 + RUN)
+        sel = got[(got["k"] >= k0) & (got["k"] < k0 + RUN)]
+        assert len(sel) == len(ref), (k0, len(sel), len(ref))
+        for key in ("x", "y", "k", "n_cov"):
+            assert np.array_equal(sel[key], ref[key]), (k0, key)
+        assert np.array_equal(sel["stack"], ref["stack"].astype(np.float32)), k0
+        assert np.array_equal(sel["snr"], ref["snr"].astype(np.float32)), k0
+        total += len(ref)
+    return total
+
+
+def check_points(got, cube, d, n_points=N_POINTS, seed=5):
+    """Sampled candidates re-evaluated point by point by the oracle's rule."""
+    rng = np.random.default_rng(seed)
+    c = got[np.sort(rng.choice(len(got), min(n_points, len(got)), replace=False))]
+    xyk = np.stack([c["x"], c["y"], c["k"]], axis=1)
+    ok, S, Cv, snr = oracle.candidates_at(cube, d["times"], d["field"], xyk, prec="fp32")
+    assert np.all(ok)
+    assert np.array_equal(c["stack"], S.astype(np.float32))
+    assert np.array_equal(c["n_cov"], Cv)
+    assert np.array_equal(c["snr"], snr.astype(np.float32))
+    return len(c)
+
+
+def window_points(d, r_xy=2, r_v=1):
+    """Every (x, y, k) within r_xy px of an injected mover's position at t_ref
+    and r_v grid steps of its velocity, in (k, y, x) order, and the number of
+    movers with a window."""
+    f = d["field"]
+    W, H, nvx, nvy = f["width"], f["height"], f["nvx"], f["nvy"]
+    pts = set()
+    for m in d["truth"]:
+        a, b, _ = synth.velocity_index(f, m[2], m[3])
+        x0, y0 = int(round(m[0])), int(round(m[1]))
+        for bb in range(max(b - r_v, 0), min(b + r_v, nvy - 1) + 1):
+            for aa in range(max(a - r_v, 0), min(a + r_v, nvx - 1) + 1):
+                for y in range(max(y0 - r_xy, 0), min(y0 + r_xy, H - 1) + 1):
+                    for x in range(max(x0 - r_xy, 0), min(x0 + r_xy, W - 1) + 1):
+                        pts.add((x, y, bb * nvx + aa))
+    return np.array(sorted(pts, key=lambda p: (p[2], p[1], p[0])), np.int64).reshape(-1, 3)
+
+
+def check_windows(got, cube, d, pts):
+    """The GPU's candidates among pts equal the oracle's, point by point;
+    returns how many there are."""
+    ok, S, Cv, snr = oracle.candidates_at(cube, d["times"], d["field"], pts, prec="fp32")
+    want = pts[ok]
+    sel = got[np.isin(_key(got["x"], got["y"], got["k"]), _key(pts[:, 0], pts[:, 1], pts[:, 2]))]
+    assert np.array_equal(_key(sel["x"], sel["y"], sel["k"]),
+                          _key(want[:, 0], want[:, 1], want[:, 2]))
+    assert np.array_equal(sel["stack"], S[ok].astype(np.float32))
+    assert np.array_equal(sel["n_cov"], Cv[ok])
+    assert np.array_equal(sel["snr"], snr[ok].astype(np.float32))
+    return len(want)
+
+
+def test_fullsize_search_planes_and_sampled_candidates(st, field, found):
+    d, cube, _, _ = field
+    got, used = found
+    assert used == 1, "the headline field must run on the register-window kernel"
+    assert len(got) > 0 and np.all(got["field"] == 0)
+    assert np.all(np.diff(_key(got["x"], got["y"], got["k"])) > 0), \
+        "candidates sorted by (k, y, x), without duplicates"
+    assert check_planes(got, cube, d, plane_runs(d)) > 0
+    assert check_points(got, cube, d) == min(N_POINTS, len(got))
+
+
+def test_fullsize_mover_windows(st, field, found):
+    d, cube, _, _ = field
+    got, _ = found
+    # the bright movers are detected: the windows hold candidates
+    assert check_windows(got, cube, d, window_points(d)) >= len(d["truth"]) // 2
+
+
+def test_fullsize_normalisation(st, field):
+    d, cube, mu, sd = field
+    raw = torch.from_numpy(np.ascontiguousarray(d["frames"])).cuda()
+    with st.Plan(d["field"], storage="f32", normalize=True, cr_clip=CR_CLIP) as p:
+        gcube, gmu, gsd = p.normalize(0, raw)
+    del raw
+    assert np.all(np.abs(gsd - sd) <= 1e-12 * sd)
+    assert np.all(np.abs(gmu - mu) <= 1e-12 * sd)
+    g = gcube.cpu().numpy()
+    del gcube
+    torch.cuda.empty_cache()
+    for i in range(0, g.shape[0], 16):  # frame blocks keep the temporaries small
+        a, b = g[i:i + 16], cube[i:i + 16]
+        tol = np.maximum(np.spacing(np.abs(b)), np.float32(1e-12))
+        assert np.all(np.abs(a - b) <= tol), i
