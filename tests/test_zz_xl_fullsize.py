@@ -17,6 +17,13 @@ parity tests (readings of Sec. 2.1 of Burdanov, Hasler & de Wit 2023):
   the same stack, coverage and S/N bit for bit;
 * mover windows: around every injected mover (+-2 px, +-1 grid step in each
   velocity axis) the GPU's candidates equal the oracle's, point by point;
+* front end (the benchmark's configuration: median removal over groups of
+  50 frames overlapping by 5, sums of every 13 frames, 2 x 2 binning): sums
+  and binning compared whole, medians on 20000 sampled pixels of every
+  group, bit for bit;
+* refinement: 4096 candidates on the 2048^2 x 300-frame field, 128 of them
+  against the FP64 oracle (J, S/N, adjoint) with the small-size bars plus
+  the derived effect of the FP32 shift at shifts of up to 208 px;
 * normalisation of the raw cube: sigma within 1e-12 relative, mu within
   1e-12 sigma (the noise frames have no sky level, so mu is near zero), and
   every output within 1 ulp of the oracle's or 1e-12 in sigma units (an
@@ -25,7 +32,7 @@ parity tests (readings of Sec. 2.1 of Burdanov, Hasler & de Wit 2023):
 
 The oracle normalises the raw frames (with the cosmic-ray clip at 10 sigma)
 and the GPU search runs on that cube, so both sides stack the same input.
-The file is named to be collected last: it takes about two minutes.
+The file is named to be collected last: it takes a few minutes.
 """
 import numpy as np
 import pytest
@@ -183,3 +190,143 @@ def test_fullsize_normalisation(st, field):
         a, b = g[i:i + 16], cube[i:i + 16]
         tol = np.maximum(np.spacing(np.abs(b)), np.float32(1e-12))
         assert np.all(np.abs(a - b) <= tol), i
+
+
+# ------------------------------------------------------------------ front end
+
+FRONT_GROUP, FRONT_OVERLAP, FRONT_SUM = 50, 5, 13  # the benchmark's front-end configuration
+N_PIX = 20000  # sampled pixels per median group
+
+
+def test_fullsize_front_end(st, field):
+    """Median removal over overlapping groups of 50 frames, sums of every 13
+    frames and 2 x 2 binning of the raw 2048^2 x 256 cube: sums and binning
+    compared whole, the medians on sampled pixels (the numpy oracle selects
+    per pixel), all bit for bit."""
+    from oracle import front
+    from paper_2303_07293_gb300 import groups as grp
+    d = field[0]
+    fr = d["frames"]
+    N, H, W = fr.shape
+    frames = torch.from_numpy(np.ascontiguousarray(fr)).cuda()
+    sums, ts = st.sum_frames(frames, d["times"], FRONT_SUM)
+    osums, ots = front.sum_frames(fr, d["times"], FRONT_SUM)
+    assert np.array_equal(sums.cpu().numpy(), osums, equal_nan=True)
+    assert np.array_equal(ts, ots)
+    del sums, osums
+    binned = st.bin2x2(frames)
+    assert np.array_equal(binned.cpu().numpy(), front.bin2x2(fr), equal_nan=True)
+    del binned
+    rng = np.random.default_rng(13)
+    pix = np.sort(rng.choice(H * W, N_PIX, replace=False))
+    pix_t = torch.from_numpy(pix).cuda()
+    flat = fr.reshape(N, H * W)
+    for s, e in grp.group_ranges(N, FRONT_GROUP, FRONT_OVERLAP):
+        out, med = st.median_subtract(frames[s:e], with_median=True)
+        got = out.reshape(e - s, H * W).index_select(1, pix_t).cpu().numpy()
+        gmed = med.reshape(H * W).index_select(0, pix_t).cpu().numpy()
+        ref, rmed = front.median_subtract(flat[s:e, pix][:, None, :])
+        assert np.array_equal(gmed, rmed[0], equal_nan=True), (s, e)
+        assert np.array_equal(got, ref[:, 0, :], equal_nan=True), (s, e)
+        del out, med
+    del frames
+    torch.cuda.empty_cache()
+
+
+# ------------------------------------------------------------------ refinement
+
+REFINE_N = 4096     # candidates per call, as benchmarked
+REFINE_SAMPLE = 128  # of them re-evaluated by the FP64 oracle
+KINK_MARGIN = 1e-4   # > FP32 error of v dt (|v dt| <= 208 px: about 2.5e-5 px)
+
+
+def refine_thetas(d, n, seed=9):
+    """theta rows (vx, vy, x0, y0, F): the injected movers first, then random
+    motions over the search grid's range and positions over the whole frame
+    (cutouts hanging over the borders included); FP64 copies of the FP32
+    values the GPU receives, and the integer cutout centres."""
+    f = d["field"]
+    rng = np.random.default_rng(seed)
+    tr = np.asarray(d["truth"], np.float64)[:, [2, 3, 0, 1, 4]]
+    m = min(len(tr), n)
+    th = np.empty((n, 5))
+    th[:m] = tr[:m]
+    k = n - m
+    th[m:, 0] = rng.uniform(f["vx0"], f["vx0"] + (f["nvx"] - 1) * f["dvx"], k)
+    th[m:, 1] = rng.uniform(f["vy0"], f["vy0"] + (f["nvy"] - 1) * f["dvy"], k)
+    th[m:, 2] = rng.uniform(0.0, f["width"] - 1.0, k)
+    th[m:, 3] = rng.uniform(0.0, f["height"] - 1.0, k)
+    th[m:, 4] = rng.uniform(0.5, 3.0, k)
+    th = th.astype(np.float32).astype(np.float64)
+    return th, np.rint(th[:, 2:4]).astype(np.int32)
+
+
+def kink_free(th, dt, margin=KINK_MARGIN):
+    """True where no frame's shift v dt (either axis) lies within margin of an
+    integer, so FP32 and FP64 pick the same bilinear cell in every frame (the
+    derivative in v jumps between cells); frames at dt = 0 shift by exactly 0
+    on both sides."""
+    d = dt[dt != 0]
+    ok = np.ones(len(th), bool)
+    for ax in (0, 1):
+        s = th[:, ax][:, None] * d[None, :]
+        fr_ = s - np.floor(s)
+        ok &= np.all((fr_ > margin) & (fr_ < 1.0 - margin), axis=1)
+    return ok
+
+
+def shift_rounding_sd(th, dt, fwhm=3.0):
+    """Standard deviations of the differences that the FP32 shift makes in J,
+    S/N and the gradient.  The kernel forms v dt in FP32 (dt rounded, then
+    the product), so a sample moves by up to |v dt| 2^-23 per axis.  For
+    unit-variance frames that changes a bilinear sample by the move times a
+    first difference (standard deviation sqrt 2) and a slope by the move
+    times a mixed second difference (standard deviation 2); the cutout
+    weights them by g (sqrt(sum g^2) = sqrt(pi) s), the velocity gradient
+    also by dt_i."""
+    s = fwhm / (2.0 * np.sqrt(2.0 * np.log(2.0)))
+    gn = np.sqrt(np.pi) * s
+    move = (np.abs(th[:, 0:1]) + np.abs(th[:, 1:2])) * np.abs(dt)[None, :] * 2.0 ** -23
+    F = np.maximum(np.abs(th[:, 4]), 1.0)
+    m2 = np.sqrt(np.sum(move ** 2, axis=1))
+    sd_J = F * np.sqrt(2.0) * gn * m2
+    sd_snr = np.sqrt(2.0) * m2 / np.sqrt(len(dt))
+    sd_g = F * 2.0 * gn * np.sqrt(np.sum((np.maximum(np.abs(dt), 1.0)[None, :] * move) ** 2,
+                                         axis=1))
+    return sd_J, sd_snr, sd_g
+
+
+def test_fullsize_refine_eval(st):
+    """The refinement objective, S/N and adjoint of 4096 candidates on the
+    2048^2 x 300-frame refinement field (the benchmark's batch and cutout),
+    128 of them against the FP64 oracle with the small-size bars: J and S/N
+    within 2e-4 relative, the gradient within 2e-4 of its largest component
+    where no frame sits within 1e-4 px of a bilinear cell edge; each bar
+    plus six standard deviations of the FP32 shift's effect (shifts reach
+    208 px here, against 5 px in the small-size test)."""
+    d = synth.make_field("refine")
+    cube = oracle.normalize(d["frames"], cr_clip=CR_CLIP)[0]
+    del d["frames"]
+    f = dict(d["field"], vx0=0.0, dvx=1.0, nvx=1, vy0=0.0, dvy=1.0, nvy=1)  # search: set-up only
+    t, t_ref = d["times"], f["t_ref"]
+    th, ce = refine_thetas(d, REFINE_N)
+    frames = torch.from_numpy(cube).cuda()
+    with st.Plan(f) as p:
+        p.candidates(frames, t)
+        J, snr, g = p.refine_eval(torch.tensor(th, dtype=torch.float32).cuda(), ce)
+        J, snr, g = J.cpu().numpy(), snr.cpu().numpy(), g.cpu().numpy()
+    del frames
+    torch.cuda.empty_cache()
+    assert np.all(np.isfinite(J)) and np.all(np.isfinite(snr)) and np.all(np.isfinite(g))
+    rng = np.random.default_rng(17)
+    idx = np.concatenate([np.arange(32), 32 + np.sort(rng.choice(REFINE_N - 32,
+                                                                 REFINE_SAMPLE - 32,
+                                                                 replace=False))])
+    oJ, osnr, og = oracle.refine_eval(cube, t, t_ref, th[idx], ce[idx])
+    sd_J, sd_snr, sd_g = shift_rounding_sd(th[idx], t - t_ref)
+    assert np.all(np.abs(J[idx] - oJ) <= 2e-4 * (np.abs(oJ) + 1.0) + 6.0 * sd_J)
+    assert np.all(np.abs(snr[idx] - osnr) <= 2e-4 * (np.abs(osnr) + 1.0) + 6.0 * sd_snr)
+    smooth = kink_free(th[idx], t - t_ref)
+    assert smooth.sum() >= REFINE_SAMPLE // 2
+    tol = 2e-4 * (np.abs(og).max(axis=1, keepdims=True) + 1.0) + 6.0 * sd_g[:, None]
+    assert np.all((np.abs(g[idx] - og) <= tol)[smooth])
