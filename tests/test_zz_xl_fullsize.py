@@ -24,6 +24,9 @@ parity tests (readings of Sec. 2.1 of Burdanov, Hasler & de Wit 2023):
 * refinement: 4096 candidates on the 2048^2 x 300-frame field, 128 of them
   against the FP64 oracle (J, S/N, adjoint) with the small-size bars plus
   the derived effect of the FP32 shift at shifts of up to 208 px;
+* the 1024^2 x 64-frame field with its 161^2 grid, nearest (as above) and
+  bilinear (values within 1e-5 max(|S64|, sqrt N) of the FP64 oracle, list
+  differences only at near-ties);
 * normalisation of the raw cube: sigma within 1e-12 relative, mu within
   1e-12 sigma (the noise frames have no sky level, so mu is near zero), and
   every output within 1 ulp of the oracle's or 1e-12 in sigma units (an
@@ -330,3 +333,98 @@ def test_fullsize_refine_eval(st):
     assert smooth.sum() >= REFINE_SAMPLE // 2
     tol = 2e-4 * (np.abs(og).max(axis=1, keepdims=True) + 1.0) + 6.0 * sd_g[:, None]
     assert np.all((np.abs(g[idx] - og) <= tol)[smooth])
+
+
+# ------------------------------------------------------------------ 1024^2 x 64 field
+
+@pytest.fixture(scope="module")
+def mid():
+    d = synth.make_field("mid")
+    cube = oracle.normalize(d["frames"], cr_clip=CR_CLIP)[0]
+    return d, cube
+
+
+def near_ties(cube, d, pts, mode="bilinear"):
+    """For each (x, y, k): the smallest gap, in the FP64 stack, between S and
+    its threshold or an in-frame neighbour's S, and the bar it is held to
+    (2e-5 max(|S|, sqrt N), twice the value bar: both sides may err)."""
+    f = d["field"]
+    W, H, N = f["width"], f["height"], f["n_frames"]
+    gaps, bars = [], []
+    for x, y, k in pts:
+        nb = [(x + dx, y + dy, k) for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+              if 0 <= x + dx < W and 0 <= y + dy < H]
+        S64, C64 = oracle.stack_points(cube, d["times"], f, np.array(nb, np.int32), mode=mode)
+        c = nb.index((x, y, k))
+        thr = float(np.float32(f["snr_threshold"] * np.sqrt(C64[c])))
+        gaps.append(min([abs(S64[c] - thr)] +
+                        [abs(S64[c] - S64[j]) for j in range(len(nb)) if j != c]))
+        bars.append(2e-5 * max(abs(S64[c]), np.sqrt(N)))
+    return np.array(gaps), np.array(bars)
+
+
+def check_bilinear(got, cube, d, ref, region):
+    """Bilinear candidates against the FP64 oracle's list ref over a region
+    (a boolean over got): common candidates within 1e-5 max(|S64|, sqrt N)
+    with the same coverage, every candidate of only one list a near-tie."""
+    N = d["field"]["n_frames"]
+    sel = got[region]
+    gk = _key(sel["x"], sel["y"], sel["k"])
+    rk = _key(ref["x"], ref["y"], ref["k"])
+    both_g, both_r = np.isin(gk, rk), np.isin(rk, gk)
+    assert np.array_equal(sel["n_cov"][both_g], ref["n_cov"][both_r])
+    s64 = ref["stack"][both_r]
+    assert np.all(np.abs(sel["stack"][both_g] - s64) <= 1e-5 * np.maximum(np.abs(s64), np.sqrt(N)))
+    only = [(int(r["x"]), int(r["y"]), int(r["k"])) for r in sel[~both_g]] + \
+           [(int(r["x"]), int(r["y"]), int(r["k"])) for r in ref[~both_r]]
+    if only:
+        gaps, bars = near_ties(cube, d, only)
+        assert np.all(gaps <= bars), [p for p, g_, b_ in zip(only, gaps, bars) if g_ > b_]
+    return int(both_g.sum()), len(only)
+
+
+@pytest.mark.parametrize("mode", ["nearest", "bilinear"])
+def test_fullsize_mid(st, mid, mode):
+    """The 1024^2 x 64-frame field (2 h, star blobs masked, 20 movers) with the
+    161 x 161 grid (+-40 px/h, step 0.5), in the benchmark's configuration,
+    for nearest shifts (bit-exact: whole plane runs, sampled candidates,
+    mover windows) and bilinear shifts (against the FP64 oracle: plane runs
+    and mover windows with the bilinear bars, sampled candidates' values)."""
+    d, cube = mid
+    f = d["field"]
+    frames = torch.from_numpy(cube).cuda()
+    with st.Plan(f, storage="f32", mode=mode, tile=-1, pending_capacity=1 << 24) as p:
+        got = p.candidates(frames, d["times"], capacity=1 << 22)
+        assert p.last_stack_variant(0) == 1, "the register-window kernel must run"
+    del frames
+    torch.cuda.empty_cache()
+    assert len(got) > 0 and np.all(np.diff(_key(got["x"], got["y"], got["k"])) > 0)
+    starts = plane_runs(d)
+    if mode == "nearest":
+        assert check_planes(got, cube, d, starts) > 0
+        check_points(got, cube, d)
+        assert check_windows(got, cube, d, window_points(d)) > 0
+        return
+    common = 0
+    for k0 in starts:
+        ref = oracle.search(cube, d["times"], f, mode="bilinear", prec="fp64", k_begin=k0,
+                            k_end=k0 + RUN)
+        common += check_bilinear(got, cube, d, ref, (got["k"] >= k0) & (got["k"] < k0 + RUN))[0]
+    assert common > 0
+    pts = window_points(d)
+    ok, S, Cv, snr = oracle.candidates_at(cube, d["times"], f, pts, mode="bilinear",
+                                          prec="fp64")
+    want = pts[ok]
+    ref = np.zeros(len(want), dtype=[("x", np.int32), ("y", np.int32), ("k", np.int32),
+                                      ("n_cov", np.int32), ("stack", np.float64)])
+    ref["x"], ref["y"], ref["k"] = want[:, 0], want[:, 1], want[:, 2]
+    ref["n_cov"], ref["stack"] = Cv[ok], S[ok]
+    region = np.isin(_key(got["x"], got["y"], got["k"]), _key(pts[:, 0], pts[:, 1], pts[:, 2]))
+    check_bilinear(got, cube, d, ref, region)
+    rng = np.random.default_rng(5)
+    c = got[np.sort(rng.choice(len(got), min(N_POINTS, len(got)), replace=False))]
+    S64, C64 = oracle.stack_points(cube, d["times"], f,
+                                   np.stack([c["x"], c["y"], c["k"]], axis=1), mode="bilinear")
+    assert np.array_equal(c["n_cov"], C64)
+    assert np.all(np.abs(c["stack"] - S64) <=
+                  1e-5 * np.maximum(np.abs(S64), np.sqrt(f["n_frames"])))
