@@ -24,7 +24,9 @@ parity tests (readings of Sec. 2.1 of Burdanov, Hasler & de Wit 2023):
 * refinement: 4096 candidates on the 2048^2 x 300-frame field, 128 of them
   against the FP64 oracle (J, S/N, adjoint) with the small-size bars plus
   the derived effect of the FP32 shift at shifts of up to 208 px;
-* the 1024^2 x 64-frame field with its 161^2 grid, nearest (as above) and
+* the 1024^2 x 64-frame field with its 161^2 grid, nearest (as above, for
+  FP32 storage and for FP16 / BF16 storage against the oracle on the frames
+  rounded to the storage type) and
   bilinear (values within 1e-5 max(|S64|, sqrt N) of the FP64 oracle, list
   differences only at near-ties);
 * normalisation of the raw cube: sigma within 1e-12 relative, mu within
@@ -383,17 +385,22 @@ def check_bilinear(got, cube, d, ref, region):
     return int(both_g.sum()), len(only)
 
 
-@pytest.mark.parametrize("mode", ["nearest", "bilinear"])
-def test_fullsize_mid(st, mid, mode):
+@pytest.mark.parametrize("mode,storage", [("nearest", "f32"), ("bilinear", "f32"),
+                                          ("nearest", "f16"), ("nearest", "bf16")])
+def test_fullsize_mid(st, mid, mode, storage):
     """The 1024^2 x 64-frame field (2 h, star blobs masked, 20 movers) with the
     161 x 161 grid (+-40 px/h, step 0.5), in the benchmark's configuration,
     for nearest shifts (bit-exact: whole plane runs, sampled candidates,
-    mover windows) and bilinear shifts (against the FP64 oracle: plane runs
-    and mover windows with the bilinear bars, sampled candidates' values)."""
-    d, cube = mid
+    mover windows; FP16 / BF16 storage against the oracle on the frames
+    rounded to the storage type) and bilinear shifts (against the FP64
+    oracle: plane runs and mover windows with the bilinear bars, sampled
+    candidates' values)."""
+    d, cube32 = mid
     f = d["field"]
-    frames = torch.from_numpy(cube).cuda()
-    with st.Plan(f, storage="f32", mode=mode, tile=-1, pending_capacity=1 << 24) as p:
+    cube = {"f32": lambda c: c, "f16": lambda c: c.astype(np.float16).astype(np.float32),
+            "bf16": oracle.round_bf16}[storage](cube32)
+    frames = torch.from_numpy(cube32).cuda()
+    with st.Plan(f, storage=storage, mode=mode, tile=-1, pending_capacity=1 << 24) as p:
         got = p.candidates(frames, d["times"], capacity=1 << 22)
         assert p.last_stack_variant(0) == 1, "the register-window kernel must run"
     del frames
