@@ -230,13 +230,20 @@ void tune_store(const std::string& path, const std::string& key, int variant) {
     while ((n = fread(buf, 1, sizeof buf, fh)) > 0) txt.append(buf, n);
     fclose(fh);
   }
-  size_t close = txt.rfind('}');
   char entry[256];
   snprintf(entry, sizeof entry, "\"%s\": %d", key.c_str(), variant);
-  if (close == std::string::npos || txt.find('"') == std::string::npos)
+  const size_t at = txt.find("\"" + key + "\"");
+  const size_t close = txt.rfind('}');
+  if (at != std::string::npos) {
+    // the key is there with a value this build cannot use: replace the value
+    const size_t end = txt.find_first_of(",}", at);
+    if (end == std::string::npos) return;
+    txt = txt.substr(0, at) + entry + txt.substr(end);
+  } else if (close == std::string::npos || txt.find('"') == std::string::npos) {
     txt = std::string("{") + entry + "}\n";
-  else
+  } else {
     txt = txt.substr(0, close) + ", " + entry + "}\n";
+  }
   if (FILE* fh = fopen(path.c_str(), "w")) {
     fputs(txt.c_str(), fh);
     fclose(fh);
