@@ -220,6 +220,15 @@ def field_for(args, rank, world):
     return synth.make_field(w, seed=base + 100000 * rank, **kw), None
 
 
+def l2_statement(ds, storage):
+    """How the timed steps stand to the 129 MB L2: the cube the stack kernel
+    reads (every field of the rank, in the storage type) against it."""
+    mb = sum(x["frames"].size for x in ds) * (4 if storage == "f32" else 2) / 1e6
+    if mb > 129.0:
+        return f"inputs larger than L2 (stored frame cube {mb:.0f} MB > 129 MB)"
+    return f"inputs smaller than L2 (stored frame cube {mb:.1f} MB): steps reuse L2"
+
+
 def precision_report(args, d, cand):
     """Stack error of the reported candidates against the FP64 oracle on the
     same normalised frames (so FP16/BF16 storage rounding is included), in
@@ -550,8 +559,7 @@ def main():
     config = {"workload": f"{args.workload}: {desc}", "frames": N, "height": H, "width": W,
               "nv": [f["nvx"], f["nvy"]], "storage": args.storage, "shift": args.mode,
               "normalize": bool(args.normalize), "cr_clip": args.cr_clip, "tau": f["snr_threshold"],
-              "tile": args.tile, "graph": bool(args.graph),
-              "l2": "inputs larger than L2 (frame cube > 129 MB)"}
+              "tile": args.tile, "graph": bool(args.graph), "l2": l2_statement(ds, args.storage)}
     if batch_total is not None:
         config.update({"fields": BATCH, "fields_this_rank": len(ds),
                        "frames": [x["frames"].shape[0] for x in ds],

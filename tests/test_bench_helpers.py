@@ -40,3 +40,15 @@ def test_precision_report_on_oracle_candidates():
     rep = bench.precision_report(args, d, c)
     assert rep["points"] == len(c) and rep["err_max_rel"] < 1e-6
     assert rep["recovered"] == rep["movers"] == 3
+
+
+def test_l2_statement_follows_the_stored_cube():
+    class Cube:  # only the element count matters
+        def __init__(self, n):
+            self.size = n
+    head = [{"frames": Cube(256 * 2048 * 2048)}]
+    assert bench.l2_statement(head, "f32") == \
+        "inputs larger than L2 (stored frame cube 4295 MB > 129 MB)"
+    assert bench.l2_statement(head, "bf16").startswith("inputs larger than L2 (stored frame cube 2147")
+    tiny = [{"frames": Cube(16 * 128 * 128)}]
+    assert bench.l2_statement(tiny, "f16").startswith("inputs smaller than L2")
