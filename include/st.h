@@ -153,8 +153,9 @@ const char* st_last_error(void);
  * allocates it on the current device and picks the stack tile variant.
  * cuda_stream: a cudaStream_t (NULL = legacy default stream) on which every
  * later call on this plan is ordered.  Limits: width, height <= 16384,
- * n_frames <= 65536, nvx*nvy <= 2^26, n_fields <= 255.  On failure *out is
- * NULL and nothing is left allocated. */
+ * n_frames <= 65535 (one grid row per frame in the normalisation kernels),
+ * nvx*nvy <= 2^26, n_fields <= 255.  On failure *out is NULL and nothing is
+ * left allocated. */
 st_status st_plan(const st_field* fields, int32_t n_fields, const st_opts* opts,
                   void* cuda_stream, st_plan_t** out);
 

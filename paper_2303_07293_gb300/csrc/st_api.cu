@@ -168,8 +168,8 @@ void free_plan(st_plan_t* p) {
 st_status validate_field(const st_field& f, int idx) {
   if (f.width <= 0 || f.height <= 0 || f.width > 16384 || f.height > 16384)
     return fail(ST_ERR_INVALID, "field %d: width/height must be in [1, 16384]", idx);
-  if (f.n_frames <= 0 || f.n_frames > 65536)
-    return fail(ST_ERR_INVALID, "field %d: n_frames must be in [1, 65536]", idx);
+  if (f.n_frames <= 0 || f.n_frames > 65535)  // frames index grid rows (at most 65535)
+    return fail(ST_ERR_INVALID, "field %d: n_frames must be in [1, 65535]", idx);
   if (f.nvx <= 0 || f.nvy <= 0 || (int64_t)f.nvx * f.nvy > (1ll << 26))
     return fail(ST_ERR_INVALID, "field %d: nvx, nvy >= 1 and nvx*nvy <= 2^26", idx);
   if (!std::isfinite(f.t_ref) || !std::isfinite(f.vx0) || !std::isfinite(f.dvx) ||

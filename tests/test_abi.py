@@ -50,6 +50,13 @@ def test_invalid_arguments_are_rejected_without_gpu_work():
     bad2 = st.Field(8, 8, 4, 0.0, 0.0, 1.0, 1, 0.0, 1.0, 1, 5.0, 9)
     assert L.st_plan(C.byref(bad2), 1, C.byref(opts), None, C.byref(h)) == st.ST_ERR_INVALID
     assert b"min_coverage" in L.st_last_error()
+    for n_frames in (0, 65536):   # frames index grid rows: at most 65535
+        bad3 = st.Field(8, 8, n_frames, 0.0, 0.0, 1.0, 1, 0.0, 1.0, 1, 5.0, 0)
+        assert L.st_plan(C.byref(bad3), 1, C.byref(opts), None, C.byref(h)) == st.ST_ERR_INVALID
+        assert b"n_frames" in L.st_last_error()
+    big = st.Field(8, 8, 4, 0.0, 0.0, 1.0, 8193, 0.0, 1.0, 8193, 5.0, 0)  # 8193^2 > 2^26
+    assert L.st_plan(C.byref(big), 1, C.byref(opts), None, C.byref(h)) == st.ST_ERR_INVALID
+    assert b"nvx*nvy" in L.st_last_error()
     good = st.Field(8, 8, 4, 0.0, 0.0, 1.0, 1, 0.0, 1.0, 1, 5.0, 0)
     bad_opts = st.Opts(7, 0, 0, 0.0, 0, 0, None, 0)
     assert L.st_plan(C.byref(good), 1, C.byref(bad_opts), None, C.byref(h)) == st.ST_ERR_INVALID
