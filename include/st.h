@@ -205,7 +205,8 @@ st_status st_stack_search_host(st_plan_t* plan, const float* const* h_frames,
  * y0, F).  Requires a prior st_stack_search on the plan (frames resident).
  * The frames are staged per candidate by TMA tile copies: returns
  * ST_ERR_UNSUPPORTED when a field's row (width x element size) is not a
- * multiple of 16 bytes or it has more than 8192 frames, and ST_ERR_TIMEOUT
+ * multiple of 16 bytes, it has more than 8192 frames or n exceeds 2^31 - 1
+ * (one thread block per candidate), and ST_ERR_TIMEOUT
  * when a copy does not land within 2 s (the kernel exits cleanly).
  * Synchronises the plan's stream. */
 st_status st_refine(st_plan_t* plan, const st_candidate* d_in, int64_t n,

@@ -907,6 +907,7 @@ st_status st_refine(st_plan_t* p, const st_candidate* d_in, int64_t n, int32_t s
   if (!(fwhm > 0.0f) || !std::isfinite(fwhm) || !std::isfinite(lr_pos) || !std::isfinite(lr_vel))
     return fail(ST_ERR_INVALID, "fwhm > 0 and finite learning rates required");
   if (optimizer != 0) return fail(ST_ERR_UNSUPPORTED, "only optimizer 0 (Adam) is built");
+  if (n > 0x7fffffffll) return fail(ST_ERR_UNSUPPORTED, "at most 2^31 - 1 candidates per call");
   if (!p->has_search) return fail(ST_ERR_INVALID, "st_refine needs a prior st_stack_search");
   if (n == 0) return ST_OK;
   return run_refine(p, true, nullptr, nullptr, nullptr, d_in, n, steps, fwhm, lr_pos, lr_vel,
@@ -920,6 +921,7 @@ st_status st_refine_eval(st_plan_t* p, const float* d_theta, const int32_t* d_ce
   if (n < 0 || (n > 0 && (!d_theta || !d_centre || !d_field || !d_J || !d_snr)))
     return fail(ST_ERR_INVALID, "n >= 0 and theta, centre, field, J, snr non-NULL");
   if (!(fwhm > 0.0f) || !std::isfinite(fwhm)) return fail(ST_ERR_INVALID, "fwhm must be > 0");
+  if (n > 0x7fffffffll) return fail(ST_ERR_UNSUPPORTED, "at most 2^31 - 1 candidates per call");
   if (!p->has_search) return fail(ST_ERR_INVALID, "st_refine_eval needs a prior st_stack_search");
   if (n == 0) return ST_OK;
   return run_refine(p, false, d_theta, d_centre, d_field, nullptr, n, 0, fwhm, 0.0f, 0.0f, d_J,
