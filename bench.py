@@ -702,12 +702,23 @@ def main():
     tr = STACK_TRAFFIC.get((args.workload, args.storage, args.mode))
     traffic = tr[0] if tr and tr[1] == stack_source_sha() and stack_launch == args.steps \
         else None
+    if traffic is not None:
+        traffic_note = "DRAM bytes of one launch from the stored ncu capture of this code"
+    elif tr is None:
+        traffic_note = "null: no ncu DRAM capture stored for this workload"
+    elif tr[1] != stack_source_sha():
+        traffic_note = (f"null: the stored capture ({tr[0] / 1e9:.2f} GB per launch) was taken "
+                        f"on k_stack_fast.cu code {tr[1]}, the kernel is now "
+                        f"{stack_source_sha()}")
+    else:
+        traffic_note = "null: the stored capture is of one launch per step"
     # algorithmic work per pixel*frame*velocity: 1 add (nearest), 4 FMA (bilinear)
     per_unit = 4.0 if args.mode == "bilinear" else 1.0
     achieved = per_unit * adds / (stack_ms / 1e3 / args.steps) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_t,
             "unit": "T FMA/s" if args.mode == "bilinear" else "T adds/s",
-            "frac": achieved / peak_t, "traffic": traffic, "work_per_unit": per_unit,
+            "frac": achieved / peak_t, "traffic": traffic, "traffic_note": traffic_note,
+            "work_per_unit": per_unit,
             "kernel": "stack (shift-and-stack + threshold)", "launches_per_step":
                 stack_launch / args.steps, "avg_launch_ms": stack_avg_ms,
             "peak_basis": f"{sms} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz (max SM clock)"}
