@@ -5,6 +5,7 @@ import ctypes as C
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -88,3 +89,21 @@ def test_new_entry_points_validate_arguments_without_gpu_work():
     d = C.c_double()
     assert L.st_probe_wait_timeout(0, C.byref(f), C.byref(d)) == st.ST_ERR_INVALID
     assert L.st_probe_wait_timeout(3000000, C.byref(f), C.byref(d)) == st.ST_ERR_INVALID
+
+
+def test_binding_rejects_host_tensors_before_the_library():
+    # the binding's marshalling checks run before any library call: CPU
+    # tensors (or wrong dtypes / layouts) never reach the C ABI
+    import torch
+    import paper_2303_07293_gb300 as st
+    cpu = torch.zeros((4, 8, 8), dtype=torch.float32)
+    with pytest.raises(ValueError):
+        st.median_subtract(cpu)
+    with pytest.raises(ValueError):
+        st.sum_frames(cpu, np.arange(4.0), 2)
+    with pytest.raises(ValueError):
+        st.bin2x2(cpu)
+    with pytest.raises(ValueError):
+        st.search_noalloc(dict(width=8, height=8, n_frames=4, t_ref=0.0, vx0=0.0, dvx=1.0,
+                               nvx=1, vy0=0.0, dvy=1.0, nvy=1, snr_threshold=5.0),
+                          cpu, np.arange(4.0))
