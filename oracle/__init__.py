@@ -44,6 +44,8 @@ def lib():
         L.oracle_num_threads.restype = C.c_int
         L.oracle_refine_eval.argtypes = [P, C.c_int, C.c_int, C.c_int, P, C.c_double, P, P,
                                          C.c_int64, C.c_double, P, P, P]
+        L.oracle_refine_gn_matrix.argtypes = [C.c_int, P, C.c_double, P, P, C.c_int64,
+                                              C.c_double, P]
         _lib = L
     return _lib
 
@@ -221,3 +223,39 @@ def refine_eval(frames, t, t_ref, theta, centre, fwhm=3.0, grad=True):
     lib().oracle_refine_eval(_p(frames), N, H, W, _p(t), float(t_ref), _p(th), _p(ce), n,
                              float(fwhm), _p(J), _p(snr), _p(g) if grad else None)
     return J, snr, g
+
+
+def refine_gn_matrix(t, t_ref, theta, centre, fwhm=3.0):
+    """Gauss-Newton curvature J^T J [n][5][5] of the refinement objective at
+    theta (order vx, vy, x0, y0, F; refine_oracle.c states the entries)."""
+    t = _f64(t)
+    th = _f64(theta).reshape(-1, 5)
+    ce = np.ascontiguousarray(centre, np.int32).reshape(-1, 2)
+    n = len(th)
+    H = np.zeros((n, 5, 5))
+    lib().oracle_refine_gn_matrix(len(t), _p(t), float(t_ref), _p(th), _p(ce), n, float(fwhm),
+                                  _p(H))
+    return H
+
+
+def refine_gn_step(frames, t, t_ref, theta, centre, fwhm=3.0, damping=0.0):
+    """One Gauss-Newton step of the refinement with the flux profiled out, in
+    the order the library's refinement takes a step: F is first set to its
+    optimum <g,S>/(N <g,g>) at the current motion and position, then
+    (vx, vy, x0, y0) move by the solution of
+        (Hs + damping diag(Hs)) delta = dJ/d(vx, vy, x0, y0),
+    Hs the Schur complement of the F entry in J^T J (the curvature of J with
+    F at its optimum).  Returns the new theta rows."""
+    th = _f64(theta).reshape(-1, 5).copy()
+    N = len(t)
+    H0 = refine_gn_matrix(t, t_ref, th, centre, fwhm)
+    J, snr, _ = refine_eval(frames, t, t_ref, th, centre, fwhm, grad=False)
+    gg = H0[:, 4, 4] / N
+    th[:, 4] = snr * np.sqrt(N * gg) / (N * gg)          # <g,S> / (N <g,g>)
+    _, _, g = refine_eval(frames, t, t_ref, th, centre, fwhm)
+    H = refine_gn_matrix(t, t_ref, th, centre, fwhm)
+    Hs = H[:, :4, :4] - H[:, :4, 4:5] * H[:, 4:5, :4] / H[:, 4:5, 4:5]
+    A = Hs + damping * Hs * np.eye(4)[None]
+    delta = np.linalg.solve(A, g[:, :4, None])[:, :, 0]
+    th[:, :4] += delta
+    return th

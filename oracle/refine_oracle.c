@@ -22,6 +22,10 @@
  * Pinned by tests/test_refine_oracle.py: closed forms for a noiseless mover
  * (F_hat = A, zero position gradient at the truth), a linear ramp (exact
  * velocity derivative), and central finite differences away from kinks.
+ * The Gauss-Newton curvature below is pinned there too: it equals the
+ * finite-difference Hessian of J at a zero-residual fit (position and flux),
+ * the motion-position coupling of the bilinear stack within 15 %, and damped
+ * steps reach a noiseless mover's parameters.
  */
 #include <math.h>
 #include <stdint.h>
@@ -87,6 +91,63 @@ int oracle_refine_eval(const float* frames, int N, int H, int W, const double* t
       grad[5 * c + 3] = F * gyS - F * F * N * ggy;
       grad[5 * c + 4] = gS - F * N * gg;
     }
+  }
+  return 0;
+}
+
+/* Gauss-Newton curvature of the refinement objective (the optimiser the
+ * library reserves as optimizer 1).  Reading: up to a constant that does not
+ * depend on theta, J is the log-likelihood of the frames under the model
+ *   m_i(q) = F g(q - (x0, y0) - v dt_i)      (unit noise per frame pixel),
+ * sampled on the cutout in reference coordinates, so Gauss-Newton replaces
+ * -Hessian(J) by the model's J^T J summed over frames and cutout pixels:
+ *   dm_i/dx0 = F Gx,  dm_i/dvx = dt_i F Gx,  dm_i/dF = g,
+ *   Gx = dg/dx0 = g (p_x - x0) / s^2   (y likewise).
+ * With T1 = sum_i dt_i and T2 = sum_i dt_i^2 the entries are
+ *   [vx,vx] F^2 T2 <Gx,Gx>   [vx,vy] F^2 T2 <Gx,Gy>   [vy,vy] F^2 T2 <Gy,Gy>
+ *   [vx,x0] F^2 T1 <Gx,Gx>   [vx,y0] F^2 T1 <Gx,Gy>   [vy,x0] F^2 T1 <Gx,Gy>
+ *   [vy,y0] F^2 T1 <Gy,Gy>   [x0,x0] F^2 N <Gx,Gx>    [x0,y0] F^2 N <Gx,Gy>
+ *   [y0,y0] F^2 N <Gy,Gy>    [vx,F] F T1 <g,Gx>       [vy,F] F T1 <g,Gy>
+ *   [x0,F] F N <g,Gx>        [y0,F] F N <g,Gy>        [F,F] N <g,g>.
+ * theta [n][5], centre [n][2] as above; H [n][5][5] in the order (vx, vy,
+ * x0, y0, F), symmetric.  The frames do not enter. */
+int oracle_refine_gn_matrix(int N, const double* t, double t_ref, const double* theta,
+                            const int32_t* centre, int64_t n, double fwhm, double* H) {
+  const double s = fwhm / (2.0 * sqrt(2.0 * log(2.0)));
+  const double inv2s2 = 1.0 / (2.0 * s * s);
+  double T1 = 0.0, T2 = 0.0;
+  for (int i = 0; i < N; ++i) {
+    const double dt = t[i] - t_ref;
+    T1 += dt;
+    T2 += dt * dt;
+  }
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t c = 0; c < n; ++c) {
+    const double x0 = theta[5 * c + 2], y0 = theta[5 * c + 3], F = theta[5 * c + 4];
+    const int cx = centre[2 * c], cy = centre[2 * c + 1];
+    double gg = 0, xx = 0, yy = 0, xy = 0, gx_ = 0, gy_ = 0;
+    for (int w = 0; w < 64; ++w)
+      for (int u = 0; u < 64; ++u) {
+        const double ddx = (double)(cx - 32 + u) - x0, ddy = (double)(cy - 32 + w) - y0;
+        const double g = exp(-(ddx * ddx + ddy * ddy) * inv2s2);
+        const double Gx = g * ddx / (s * s), Gy = g * ddy / (s * s);
+        gg += g * g;
+        xx += Gx * Gx;
+        yy += Gy * Gy;
+        xy += Gx * Gy;
+        gx_ += g * Gx;
+        gy_ += g * Gy;
+      }
+    const double F2 = F * F;
+    double* h = H + 25 * c;
+    const double e[5][5] = {
+        {F2 * T2 * xx, F2 * T2 * xy, F2 * T1 * xx, F2 * T1 * xy, F * T1 * gx_},
+        {F2 * T2 * xy, F2 * T2 * yy, F2 * T1 * xy, F2 * T1 * yy, F * T1 * gy_},
+        {F2 * T1 * xx, F2 * T1 * xy, F2 * N * xx, F2 * N * xy, F * N * gx_},
+        {F2 * T1 * xy, F2 * T1 * yy, F2 * N * xy, F2 * N * yy, F * N * gy_},
+        {F * T1 * gx_, F * T1 * gy_, F * N * gx_, F * N * gy_, N * gg}};
+    for (int a = 0; a < 5; ++a)
+      for (int b = 0; b < 5; ++b) h[5 * a + b] = e[a][b];
   }
   return 0;
 }

@@ -89,3 +89,87 @@ def test_gradient_matches_central_differences():
         Jm, _, _ = oracle.refine_eval(fr, t, t_ref, [tm], [[55, 55]], FWHM, grad=False)
         fd = (Jp[0] - Jm[0]) / (2 * h)
         assert abs(fd - grad[0, k]) <= 1e-5 * max(1.0, abs(grad[0, k])), (k, fd, grad[0, k])
+
+
+# ------------------------------------------------ Gauss-Newton curvature (optimizer 1)
+
+def _noiseless(t, t_ref, theta, H=120, W=140):
+    """Frames of one mover with parameters theta = (vx, vy, x0, y0, A)."""
+    vx, vy, x0, y0, A = theta
+    fr = np.zeros((len(t), H, W), np.float32)
+    synth.render_movers(fr, t, t_ref, [[x0, y0, vx, vy, A]], fwhm=FWHM)
+    return fr
+
+
+def test_gauss_newton_curvature_is_the_hessian_of_a_noiseless_fit():
+    # zero residuals (a mover rendered with the template's PSF on integer
+    # shifts, at its true parameters): J^T J equals -Hessian(J) exactly in
+    # position and flux, where J is smooth; central differences of the
+    # analytic gradient give that Hessian
+    t = np.arange(9, dtype=np.float64)
+    t_ref = 3.0                                    # sum of dt != 0: couplings present
+    truth = (2.0, -1.0, 70.0, 58.0, 1.7)
+    fr = _noiseless(t, t_ref, truth)
+    th = np.array([truth])
+    ce = [[70, 58]]
+    Hm = oracle.refine_gn_matrix(t, t_ref, th, ce)[0]
+    assert np.allclose(Hm, Hm.T)
+    h = 1e-4
+    for a in (2, 3, 4):
+        tp, tm = th.copy(), th.copy()
+        tp[0, a] += h
+        tm[0, a] -= h
+        col = (oracle.refine_eval(fr, t, t_ref, tp, ce)[2][0] -
+               oracle.refine_eval(fr, t, t_ref, tm, ce)[2][0]) / (2 * h)
+        for b in (2, 3, 4):
+            assert abs(col[b] + Hm[b, a]) <= 1e-5 * abs(Hm[4, 4]), (a, b)
+    # closed forms of the isotropic template, <Gx,Gx> = pi/2 and <g,g> =
+    # pi s^2 (integrals; the cutout sums them on the pixel grid, where a
+    # Gaussian of width s/sqrt 2 = 0.9 px aliases below 1e-4)
+    N = len(t)
+    assert abs(Hm[2, 2] - 1.7 ** 2 * N * math.pi / 2) <= 1e-4 * Hm[2, 2]
+    assert abs(Hm[4, 4] - N * math.pi * SIG ** 2) <= 1e-4 * Hm[4, 4]
+    T1, T2 = float((t - t_ref).sum()), float(((t - t_ref) ** 2).sum())
+    assert abs(Hm[0, 0] - T2 / N * Hm[2, 2]) <= 1e-9 * Hm[0, 0]
+    assert abs(Hm[0, 2] - T1 / N * Hm[2, 2]) <= 1e-9 * abs(Hm[0, 2])
+
+
+def test_gauss_newton_motion_position_coupling():
+    # d/dvx (dJ/dx0) of the bilinear stack approaches -[vx, x0] of J^T J;
+    # the bilinear cell slopes of a sampled PSF (FWHM 3 px) stand in for its
+    # derivative, within 15 %
+    t = np.array([0.0, 0.7, 1.6, 2.1, 2.9, 3.3, 4.8, 5.2, 6.5, 7.9, 8.4])
+    t_ref = 2.1
+    truth = (1.37, -0.83, 70.3, 58.6, 2.0)
+    fr = _noiseless(t, t_ref, truth)
+    th = np.array([truth])
+    ce = [[70, 59]]
+    Hm = oracle.refine_gn_matrix(t, t_ref, th, ce)[0]
+    h = 1e-3
+    for a, b in ((0, 2), (1, 3)):
+        tp, tm = th.copy(), th.copy()
+        tp[0, a] += h
+        tm[0, a] -= h
+        d = (oracle.refine_eval(fr, t, t_ref, tp, ce)[2][0][b] -
+             oracle.refine_eval(fr, t, t_ref, tm, ce)[2][0][b]) / (2 * h)
+        assert abs(d + Hm[a, b]) <= 0.15 * abs(Hm[a, b]), (a, b, d, Hm[a, b])
+
+
+def test_gauss_newton_steps_approach_the_truth():
+    # damped steps from 0.4 px (and the matching motion) off a noiseless
+    # mover settle within 0.05 of the truth in every parameter; the bilinear
+    # objective's own maximum lies about 0.01 from it
+    t = np.array([0.0, 0.7, 1.6, 2.1, 2.9, 3.3, 4.8, 5.2, 6.5, 7.9, 8.4])
+    t_ref = 2.1
+    truth = np.array([1.37, -0.83, 70.3, 58.6, 2.0])
+    fr = _noiseless(t, t_ref, truth)
+    ce = [[70, 59]]
+    th = truth[None].copy()
+    th[0, :4] += [0.4 / 6.3, -0.3 / 6.3, 0.4, -0.3]
+    errs = []
+    for _ in range(6):
+        errs.append(np.abs(th[0, :4] - truth[:4]).max())
+        th = oracle.refine_gn_step(fr, t, t_ref, th, ce, damping=1.0)
+    errs.append(np.abs(th[0, :4] - truth[:4]).max())
+    assert errs[1] < 0.6 * errs[0] and errs[2] < 0.6 * errs[1]
+    assert errs[-1] <= 0.05
