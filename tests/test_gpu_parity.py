@@ -196,6 +196,26 @@ def test_normalize_matches_oracle(st, storage):
     assert np.all(got[np.isnan(raw)] == 0.0)
 
 
+def test_normalize_degenerate_frames(st):
+    # a frame with no finite pixel and a constant frame have no sky scatter:
+    # both normalise to zeros with the oracle's mu and sigma; the ordinary
+    # frame between them is unaffected
+    d = synth.make_field("tiny")
+    raw = d["frames"][:3] * 2.0 + 5.0
+    raw[0] = np.nan
+    raw[2] = 7.25
+    f = dict(d["field"], n_frames=3)
+    with st.Plan(f, normalize=True) as p:
+        cube, mu, sd = p.normalize(0, dev(raw))
+    out, omu, osd = oracle.normalize(raw)
+    got = cube.cpu().numpy()
+    assert np.all(got[0] == 0.0) and np.all(got[2] == 0.0)
+    assert mu[0] == omu[0] == 0.0 and sd[0] == osd[0] == 0.0
+    assert mu[2] == omu[2] == 7.25 and sd[2] == osd[2] == 0.0
+    assert abs(mu[1] - omu[1]) <= 1e-12 * abs(omu[1]) and abs(sd[1] - osd[1]) <= 1e-12 * osd[1]
+    assert np.all(np.abs(got[1] - out[1]) <= np.spacing(np.abs(out[1]).astype(np.float32)))
+
+
 def test_normalized_search_finds_movers(st):
     d = synth.make_field("mid", width=256, n_frames=32, nv=41, n_movers=6)
     raw = d["frames"] * 2.0 + 100.0

@@ -101,6 +101,20 @@ def test_normalize_closed_form_nan_and_clip():
     assert good.sum() == N * H * W - 1
 
 
+def test_normalize_degenerate_frames():
+    # no finite pixel: no statistics (mu = sigma = 0); a constant frame: no
+    # scatter (sigma = 0); both map to zeros, the frame between is untouched
+    raw = np.empty((3, 5, 8), np.float32)
+    raw[0] = np.nan
+    raw[1] = np.where((np.arange(40) % 2) == 0, 3.0, 5.0).reshape(5, 8)  # mean 4, std 1
+    raw[2] = 7.25
+    out, mu, sd = oracle.normalize(raw)
+    assert mu[0] == 0.0 and sd[0] == 0.0 and np.all(out[0] == 0.0)
+    assert mu[2] == 7.25 and sd[2] == 0.0 and np.all(out[2] == 0.0)
+    assert mu[1] == 4.0 and sd[1] == 1.0
+    assert np.array_equal(out[1], raw[1] - 4.0)
+
+
 # ------------------------------------------------------ a3 nearest stacking
 
 @pytest.fixture(scope="module")
