@@ -60,6 +60,33 @@ def test_fast_dump_bitexact(st, seed, shape):
         assert np.array_equal(S.cpu().numpy(), oS.astype(np.float32)), tile
 
 
+def test_fast_degenerate_grids_and_frames(st):
+    # one velocity at rest (the stack is the plain frame sum, Sec. 2.1's
+    # zero-motion case), and a frame narrower and shorter than one tile
+    N, H, W = 12, 20, 40
+    fr = synth.noise(N, H, W, seed=31)
+    t = np.arange(N, dtype=np.float64) * 0.3
+    f0 = synth.field_params(W, H, N, float(t[5]), 0.0, 1.0, 1, 0.0, 1.0, 1, tau=2.0)
+    fr2, t2, f2 = field(32, W=12, H=5, N=10, nvx=3, nvy=2)
+    frame_sum = np.zeros((H, W), np.float32)
+    for i in range(N):
+        frame_sum = (frame_sum + fr[i]).astype(np.float32)
+    for frames, times, f in ((fr, t, f0), (fr2, t2, f2)):
+        ks = np.arange(f["nvx"] * f["nvy"], dtype=np.int32)
+        oS, oC = oracle.stack_planes(frames, times, f, ks, prec="fp32")
+        ref = oracle.search(frames, times, f, prec="fp32")
+        for tile in VARIANTS:
+            with st.Plan(f, tile=tile) as p:
+                S, Cv = p.dump_stack(0, dev(frames), times, ks)
+                got = p.candidates(dev(frames), times)
+                assert p.last_stack_variant(0) == 1, "register-window kernel not used"
+            assert np.array_equal(Cv.cpu().numpy(), oC), tile
+            assert np.array_equal(S.cpu().numpy(), oS.astype(np.float32)), tile
+            assert got[["x", "y", "k", "n_cov"]].tolist() == \
+                ref[["x", "y", "k", "n_cov"]].tolist(), tile
+    assert np.array_equal(oS[0].astype(np.float32), frame_sum)
+
+
 @pytest.mark.parametrize("seed,shape", [(5, dict()), (6, dict(W=256, H=80, N=48, nvx=33, nvy=17)),
                                         (7, dict(W=64, H=64, N=30, nvx=8, nvy=8, ref=-1))])
 def test_fast_search_equals_generic_and_oracle(st, seed, shape):
