@@ -285,6 +285,25 @@ def test_host_buffer_entry_point_matches_device(st):
         assert p.last_launch_count() > 0
 
 
+@pytest.mark.parametrize("W,H", [(16384, 8), (8, 16384)])
+def test_search_at_the_frame_size_limits(st, W, H):
+    # the largest width and height a plan accepts: coordinates near 2^14 in
+    # the packed (field, k, y, x) sort key, and a grid of many tiles along
+    # one axis; sources at both ends of the long axis
+    N = 8
+    fr = synth.noise(N, H, W, seed=40 + W % 7)
+    t = np.arange(N, dtype=np.float64)
+    f = synth.field_params(W, H, N, 4.0, -0.25, 0.25, 3, -0.25, 0.25, 3, tau=4.0)
+    far = (W - 3, 4) if W > H else (4, H - 3)
+    synth.render_movers(fr, t, 4.0, [[far[0], far[1], 0.0, 0.0, 6.0], [3.0, 3.0, 0.25, 0.0, 6.0]])
+    with st.Plan(f) as p:
+        got = p.candidates(dev(fr), t)
+    ref = oracle.search(fr, t, f, prec="fp32")
+    assert len(ref) > 0 and (ref["x"].max() >= W - 8 or ref["y"].max() >= H - 8)
+    assert got[["x", "y", "k", "n_cov"]].tolist() == ref[["x", "y", "k", "n_cov"]].tolist()
+    assert np.array_equal(got["stack"], ref["stack"].astype(np.float32))
+
+
 def test_empty_result_and_single_frame(st):
     fr = np.zeros((1, 5, 7), np.float32)
     f = synth.field_params(7, 5, 1, 0.0, -1.0, 1.0, 3, 0.0, 1.0, 1, tau=1.0)
