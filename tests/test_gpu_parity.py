@@ -304,6 +304,22 @@ def test_search_at_the_frame_size_limits(st, W, H):
     assert np.array_equal(got["stack"], ref["stack"].astype(np.float32))
 
 
+def test_search_on_the_largest_grid(st):
+    # nvx * nvy = 2^26, the largest grid a plan accepts (velocity indices up
+    # to 2^26 - 1 in the sort key), on a small field of pure noise
+    N, H, W = 8, 8, 8
+    fr = synth.noise(N, H, W, seed=77)
+    t = np.arange(N, dtype=np.float64)
+    nv = 8192
+    f = synth.field_params(W, H, N, 4.0, -0.5, 1.0 / nv, nv, -0.5, 1.0 / nv, nv, tau=4.5)
+    with st.Plan(f) as p:
+        got = p.candidates(dev(fr), t)
+    ref = oracle.search(fr, t, f, prec="fp32")
+    assert len(ref) > 0 and ref["k"].max() >= 1 << 25
+    assert got[["x", "y", "k", "n_cov"]].tolist() == ref[["x", "y", "k", "n_cov"]].tolist()
+    assert np.array_equal(got["stack"], ref["stack"].astype(np.float32))
+
+
 def test_empty_result_and_single_frame(st):
     fr = np.zeros((1, 5, 7), np.float32)
     f = synth.field_params(7, 5, 1, 0.0, -1.0, 1.0, 3, 0.0, 1.0, 1, tau=1.0)
