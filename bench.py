@@ -569,6 +569,11 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
+        if world > 1:
+            # rank 0 runs alone (the other ranks have returned): give the
+            # oracle the host's cores, which the launcher limited to one
+            import oracle
+            oracle.set_num_threads(len(os.sched_getaffinity(0)))
         if args.workload == "refine":
             return refine_reference(args, d, config)
         if args.workload == "front":

@@ -42,6 +42,8 @@ def lib():
             C.c_int, C.c_int, C.c_float, C.c_int, C.c_int32, C.c_int32, P, C.c_int64]
         L.oracle_search.restype = C.c_int64
         L.oracle_num_threads.restype = C.c_int
+        L.oracle_set_num_threads.argtypes = [C.c_int]
+        L.oracle_set_num_threads.restype = None
         L.oracle_refine_eval.argtypes = [P, C.c_int, C.c_int, C.c_int, P, C.c_double, P, P,
                                          C.c_int64, C.c_double, P, P, P]
         L.oracle_refine_gn_matrix.argtypes = [C.c_int, P, C.c_double, P, P, C.c_int64,
@@ -64,6 +66,10 @@ def _f64(a):
 
 def num_threads() -> int:
     return lib().oracle_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    lib().oracle_set_num_threads(int(n))
 
 
 def shift_tables(t, t_ref, v0, dv, nv, mode="nearest"):

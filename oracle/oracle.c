@@ -398,3 +398,14 @@ int oracle_num_threads(void) {
   return 1;
 #endif
 }
+
+/* Threads of the following parallel regions (n >= 1); no effect without
+ * OpenMP.  For a process that runs alone although its launcher limited each
+ * process to one thread. */
+void oracle_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
