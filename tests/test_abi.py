@@ -107,3 +107,45 @@ def test_binding_rejects_host_tensors_before_the_library():
         st.search_noalloc(dict(width=8, height=8, n_frames=4, t_ref=0.0, vx0=0.0, dvx=1.0,
                                nvx=1, vy0=0.0, dvy=1.0, nvy=1, snr_threshold=5.0),
                           cpu, np.arange(4.0))
+
+
+def test_header_is_c99_and_its_layouts_match_the_binding(tmp_path):
+    # the header compiles as strict C99, and every struct the binding mirrors
+    # (ctypes structures, numpy record dtypes) has the same size and field
+    # offsets as the C compiler gives it
+    import shutil
+    import subprocess
+    import paper_2303_07293_gb300 as st
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    layouts = {
+        "st_field": ([f for f, _ in st.Field._fields_], C.sizeof(st.Field),
+                     [getattr(st.Field, f).offset for f, _ in st.Field._fields_]),
+        "st_opts": ([f for f, _ in st.Opts._fields_], C.sizeof(st.Opts),
+                    [getattr(st.Opts, f).offset for f, _ in st.Opts._fields_]),
+        "st_candidate": (list(st.CAND_DTYPE.names), st.CAND_DTYPE.itemsize,
+                         [st.CAND_DTYPE.fields[n][1] for n in st.CAND_DTYPE.names]),
+        "st_track": (list(st.TRACK_DTYPE.names), st.TRACK_DTYPE.itemsize,
+                     [st.TRACK_DTYPE.fields[n][1] for n in st.TRACK_DTYPE.names]),
+        "st_refined": (list(st.REFINED_DTYPE.names),
+                       st.REFINED_DTYPE.itemsize,
+                       [st.REFINED_DTYPE.fields[n][1] for n in st.REFINED_DTYPE.names]),
+    }
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "st.h"', "int main(void) {"]
+    for t, (names, _, _) in layouts.items():
+        lines.append(f'  printf("{t} %zu", sizeof({t}));')
+        for n in names:
+            lines.append(f'  printf(" %zu", offsetof({t}, {n}));')
+        lines.append('  printf("\\n");')
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-pedantic", "-I",
+                    os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {ln.split()[0]: [int(v) for v in ln.split()[1:]] for ln in out if ln.strip()}
+    for t, (names, size, offs) in layouts.items():
+        assert got[t][0] == size, (t, got[t][0], size)
+        assert got[t][1:] == offs, (t, names, got[t][1:], offs)
