@@ -52,3 +52,29 @@ def test_l2_statement_follows_the_stored_cube():
     assert bench.l2_statement(head, "bf16").startswith("inputs larger than L2 (stored frame cube 2147")
     tiny = [{"frames": Cube(16 * 128 * 128)}]
     assert bench.l2_statement(tiny, "f16").startswith("inputs smaller than L2")
+
+
+def test_reference_arm_prints_one_contract_line():
+    # the reference arm (the CPU oracle) runs without a GPU: one JSON line
+    # with the keys of the benchmark contract, its own baseline and e2e
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                        "--workload", "tiny", "--steps", "1", "--warmup", "0",
+                        "--cpu-seconds", "1"], capture_output=True, text=True, timeout=600,
+                       cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["config"]["workload"].startswith("tiny")
