@@ -29,6 +29,9 @@ parity tests (readings of Sec. 2.1 of Burdanov, Hasler & de Wit 2023):
   rounded to the storage type) and
   bilinear (values within 1e-5 max(|S64|, sqrt N) of the FP64 oracle, list
   differences only at near-ties);
+* four fields of the 24-field batch at their full sizes in one plan (FP16
+  storage, CUDA graph, one persistent launch), each against the oracle on
+  its frames rounded to FP16, bit for bit;
 * normalisation of the raw cube: sigma within 1e-12 relative, mu within
   1e-12 sigma (the noise frames have no sky level, so mu is near zero), and
   every output within 1 ulp of the oracle's or 1e-12 in sigma units (an
@@ -435,3 +438,50 @@ def test_fullsize_mid(st, mid, mode, storage):
     assert np.array_equal(c["n_cov"], C64)
     assert np.all(np.abs(c["stack"] - S64) <=
                   1e-5 * np.maximum(np.abs(S64), np.sqrt(f["n_frames"])))
+
+
+# ------------------------------------------------------------------ batched fields
+
+BATCH_FIELDS = (23, 5, 15, 14)  # of the 24-field batch: 512^2-2048^2, 45-289 frames
+
+
+@pytest.fixture(scope="module")
+def batch():
+    base = synth.BASE_SEED + 4
+    ds = [synth.make_field("batched", seed=base, index=j) for j in BATCH_FIELDS]
+    cubes = [oracle.normalize(d["frames"], cr_clip=CR_CLIP)[0] for d in ds]
+    for d in ds:
+        del d["frames"]
+    return ds, cubes
+
+
+def test_fullsize_batched_fields_one_launch(st, batch):
+    """Four fields of the batched workload at their full sizes in one plan, in
+    the benchmark's configuration of the batch: FP16 storage, autotuned
+    variant, the device part captured in a CUDA graph and replayed, one
+    persistent launch over all fields.  Against the oracle on each field's
+    frames rounded to FP16 (the same FP32 adds, bit for bit): plane runs,
+    sampled candidates and mover windows of every field."""
+    ds, cubes = batch
+    frames = [torch.from_numpy(c).cuda() for c in cubes]
+    times = [d["times"] for d in ds]
+    with st.Plan([d["field"] for d in ds], storage="f16", mode="nearest", tile=-1,
+                 use_graph=True, pending_capacity=1 << 24) as p:
+        first = p.candidates(frames, times, capacity=1 << 22)
+        got = p.candidates(frames, times, capacity=1 << 22)
+        assert p.last_graph_replayed()
+        assert [p.last_stack_variant(i) for i in range(len(ds))] == [1] * len(ds)
+        _, stack_launches = p.last_stack_kernel_time()
+    del frames
+    torch.cuda.empty_cache()
+    assert stack_launches == 1
+    assert got.tobytes() == first.tobytes()
+    assert np.all(np.diff(got["field"]) >= 0)
+    for j, (d, c) in enumerate(zip(ds, cubes)):
+        r16 = c.astype(np.float16).astype(np.float32)
+        g = got[got["field"] == j]
+        assert len(g) > 0
+        assert np.all(np.diff(_key(g["x"], g["y"], g["k"])) > 0)
+        assert check_planes(g, r16, d, plane_runs(d)) >= 0
+        check_points(g, r16, d, n_points=500)
+        check_windows(g, r16, d, window_points(d))
