@@ -29,6 +29,7 @@ parity tests (readings of Sec. 2.1 of Burdanov, Hasler & de Wit 2023):
   rounded to the storage type) and
   bilinear (values within 1e-5 max(|S64|, sqrt N) of the FP64 oracle, list
   differences only at near-ties);
+* the multi-night workload at its full size, bit for bit;
 * four fields of the 24-field batch at their full sizes in one plan (FP16
   storage, CUDA graph, one persistent launch), each against the oracle on
   its frames rounded to FP16, bit for bit;
@@ -485,3 +486,29 @@ def test_fullsize_batched_fields_one_launch(st, batch):
         assert check_planes(g, r16, d, plane_runs(d)) >= 0
         check_points(g, r16, d, n_points=500)
         check_windows(g, r16, d, window_points(d))
+
+
+# ------------------------------------------------------------------ multi-night stack
+
+def test_fullsize_multinight():
+    """The multi-night workload at its full size (two nights of 64 frames of
+    1024^2 px 24 h apart, a grid of 1 px over the whole baseline), searched as
+    benchmarked (FP32, autotuned register-window variant): plane runs,
+    sampled candidates and mover windows bit for bit with the oracle."""
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2303_07293_gb300 as stm
+    d = synth.make_field("multinight")
+    cube = oracle.normalize(d["frames"], cr_clip=CR_CLIP)[0]
+    del d["frames"]
+    frames = torch.from_numpy(cube).cuda()
+    with stm.Plan(d["field"], storage="f32", mode="nearest", tile=-1,
+                  pending_capacity=1 << 24) as p:
+        got = p.candidates(frames, d["times"], capacity=1 << 22)
+        assert p.last_stack_variant(0) == 1
+    del frames
+    torch.cuda.empty_cache()
+    assert len(got) > 0 and np.all(np.diff(_key(got["x"], got["y"], got["k"])) > 0)
+    assert check_planes(got, cube, d, plane_runs(d)) >= 0
+    check_points(got, cube, d, n_points=1000)
+    check_windows(got, cube, d, window_points(d))
