@@ -490,20 +490,17 @@ def test_fullsize_batched_fields_one_launch(st, batch):
 
 # ------------------------------------------------------------------ multi-night stack
 
-def test_fullsize_multinight():
+def test_fullsize_multinight(st):
     """The multi-night workload at its full size (two nights of 64 frames of
     1024^2 px 24 h apart, a grid of 1 px over the whole baseline), searched as
     benchmarked (FP32, autotuned register-window variant): plane runs,
     sampled candidates and mover windows bit for bit with the oracle."""
-    import __graft_entry__
-    __graft_entry__.build()
-    import paper_2303_07293_gb300 as stm
     d = synth.make_field("multinight")
     cube = oracle.normalize(d["frames"], cr_clip=CR_CLIP)[0]
     del d["frames"]
     frames = torch.from_numpy(cube).cuda()
-    with stm.Plan(d["field"], storage="f32", mode="nearest", tile=-1,
-                  pending_capacity=1 << 24) as p:
+    with st.Plan(d["field"], storage="f32", mode="nearest", tile=-1,
+                 pending_capacity=1 << 24) as p:
         got = p.candidates(frames, d["times"], capacity=1 << 22)
         assert p.last_stack_variant(0) == 1
     del frames
