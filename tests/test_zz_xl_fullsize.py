@@ -17,6 +17,8 @@ parity tests (readings of Sec. 2.1 of Burdanov, Hasler & de Wit 2023):
   the same stack, coverage and S/N bit for bit;
 * mover windows: around every injected mover (+-2 px, +-1 grid step in each
   velocity axis) the GPU's candidates equal the oracle's, point by point;
+* the same checks with FP16 frame storage, against the oracle on the frames
+  rounded to FP16;
 * front end (the benchmark's configuration: median removal over groups of
   50 frames overlapping by 5, sums of every 13 frames, 2 x 2 binning): sums
   and binning compared whole, medians on 20000 sampled pixels of every
@@ -175,6 +177,25 @@ def test_fullsize_search_planes_and_sampled_candidates(st, field, found):
         "candidates sorted by (k, y, x), without duplicates"
     assert check_planes(got, cube, d, plane_runs(d)) > 0
     assert check_points(got, cube, d) == min(N_POINTS, len(got))
+
+
+def test_fullsize_fp16_storage(st, field):
+    # the headline search with FP16 frame storage (the plan rounds the cube
+    # to FP16, the sums stay FP32 in frame order): bit for bit with the
+    # oracle on the frames rounded to FP16, on plane runs, sampled candidates
+    # and mover windows
+    d, cube, _, _ = field
+    frames = torch.from_numpy(cube).cuda()
+    with st.Plan(d["field"], storage="f16", mode="nearest", tile=-1,
+                 pending_capacity=1 << 24) as p:
+        got = p.candidates(frames, d["times"], capacity=1 << 22)
+        assert p.last_stack_variant(0) == 1
+    del frames
+    torch.cuda.empty_cache()
+    r16 = cube.astype(np.float16).astype(np.float32)
+    assert check_planes(got, r16, d, plane_runs(d)) > 0
+    check_points(got, r16, d, n_points=1000)
+    check_windows(got, r16, d, window_points(d))
 
 
 def test_fullsize_mover_windows(st, field, found):
