@@ -75,6 +75,9 @@ def test_fast_degenerate_grids_and_frames(st):
         ks = np.arange(f["nvx"] * f["nvy"], dtype=np.int32)
         oS, oC = oracle.stack_planes(frames, times, f, ks, prec="fp32")
         ref = oracle.search(frames, times, f, prec="fp32")
+        if f is f0:
+            # the single velocity at rest: the oracle's plane is the frame sum
+            assert np.array_equal(oS[0].astype(np.float32), frame_sum)
         for tile in VARIANTS:
             with st.Plan(f, tile=tile) as p:
                 S, Cv = p.dump_stack(0, dev(frames), times, ks)
@@ -82,9 +85,10 @@ def test_fast_degenerate_grids_and_frames(st):
                 assert p.last_stack_variant(0) == 1, "register-window kernel not used"
             assert np.array_equal(Cv.cpu().numpy(), oC), tile
             assert np.array_equal(S.cpu().numpy(), oS.astype(np.float32)), tile
+            if f is f0:
+                assert np.array_equal(S.cpu().numpy()[0], frame_sum), tile
             assert got[["x", "y", "k", "n_cov"]].tolist() == \
                 ref[["x", "y", "k", "n_cov"]].tolist(), tile
-    assert np.array_equal(oS[0].astype(np.float32), frame_sum)
 
 
 @pytest.mark.parametrize("seed,shape", [(5, dict()), (6, dict(W=256, H=80, N=48, nvx=33, nvy=17)),
