@@ -195,7 +195,7 @@ st_status st_stack_search_host(st_plan_t* plan, const float* const* h_frames,
  * parameters theta = (vx, vy, x0, y0, F) start at the grid velocity, the pixel
  * and F = S/(N<g,g>); the objective on a 64x64 output cutout centred on the
  * starting pixel is
- *     J = F*<g, S_theta> - 0.5*F^2*N_cov*<g, g>,
+ *     J = F*<g, S_theta> - 0.5*F^2*N*<g, g>,
  * with S_theta the bilinear stack of the raw cube (FP32 input frames of the
  * plan's last search, normalised when the plan normalises) and g a Gaussian
  * of the given FWHM centred on (x0, y0).  `steps` optimiser steps
@@ -224,13 +224,16 @@ st_status st_refine_eval(st_plan_t* plan, const float* d_theta,
                          float* d_grad);
 
 /* Search of one field that allocates no memory (the paper has no counterpart:
- * this serves callers that cannot allocate device memory when they search,
- * such as code inside a CUDA stream capture that must not add allocation
- * nodes, or processes whose device memory is reserved up front by another
- * allocator).  Same kernels, definitions and sorted output as st_stack_search
+ * this serves callers that cannot allocate device memory when they search:
+ * processes whose device memory is reserved up front by another allocator,
+ * such as a framework's caching allocator that holds the free memory, and
+ * hosts that forbid cudaMalloc after start-up because it can synchronise the
+ * device and take unbounded time).  Same kernels, definitions and sorted output as st_stack_search
  * with normalize = 0 and FP32 storage, for one field (field index 0 in the
  * records).
- *   field      : the field (limits as st_plan); mode: ST_NEAREST or ST_BILINEAR.
+ *   field      : the field (limits as st_plan: width, height <= 16384,
+ *                n_frames <= 65535, nvx*nvy <= 2^26); mode: ST_NEAREST or
+ *                ST_BILINEAR.
  *   d_frames   : device FP32 cube [N][H][W], used as given (not normalised).
  *   h_times    : host FP64 timestamps [N].
  *   d_out      : device array of `capacity` candidates (caller-owned).

@@ -1,10 +1,9 @@
 // st_noalloc.cu — a search entry point that allocates no memory.
 //
 // Some callers cannot allocate device memory at the point where they search:
-// code running inside a CUDA stream capture that must not add allocation
-// nodes, processes whose device memory is fully reserved up front by another
-// runtime or allocator, and embedded hosts that forbid cudaMalloc after
-// start-up.  st_stack_search_noalloc serves them: it runs the same kernels as
+// processes whose device memory is fully reserved up front by another
+// runtime or allocator, and hosts that forbid cudaMalloc after start-up
+// (it can synchronise the device and take unbounded time).  st_stack_search_noalloc serves them: it runs the same kernels as
 // st_stack_search for one field, but every scratch buffer it needs (shift
 // tables, thresholds, counters, the above-threshold list, candidate records
 // and sort keys) is carved out of one file-scope device array of
@@ -90,7 +89,7 @@ extern "C" st_status st_stack_search_noalloc(const st_field* field, int32_t mode
     return na_fail(ST_ERR_INVALID, "mode must be ST_NEAREST or ST_BILINEAR");
   const st_field& f = *field;
   if (f.width <= 0 || f.height <= 0 || f.width > 16384 || f.height > 16384 || f.n_frames <= 0 ||
-      f.n_frames > 65536 || f.nvx <= 0 || f.nvy <= 0 || (int64_t)f.nvx * f.nvy > (1ll << 26) ||
+      f.n_frames > 65535 || f.nvx <= 0 || f.nvy <= 0 || (int64_t)f.nvx * f.nvy > (1ll << 26) ||
       f.min_coverage < 0 || f.min_coverage > f.n_frames || !std::isfinite(f.snr_threshold) ||
       f.snr_threshold < 0.0f || !std::isfinite(f.t_ref) || !std::isfinite(f.vx0) ||
       !std::isfinite(f.dvx) || !std::isfinite(f.vy0) || !std::isfinite(f.dvy))

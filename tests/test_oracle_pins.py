@@ -344,3 +344,89 @@ def test_candidates_sorted_by_k_then_raster():
     c = oracle.search(d["frames"], d["times"], d["field"], prec="fp32")
     key = c["k"].astype(np.int64) << 32 | c["y"].astype(np.int64) << 16 | c["x"]
     assert len(c) > 3 and np.all(np.diff(key) > 0)
+
+
+# ------------------------------------------------- a7 BF16 storage rounding
+
+def _f32_bits(u):
+    return np.array(u, dtype=np.uint32).view(np.float32)
+
+
+def _bits(x):
+    return np.asarray(x, np.float32).view(np.uint32)
+
+
+def test_round_bf16_hand_cases():
+    # A BF16 value is an FP32 value whose low 16 bits are zero; storing an
+    # FP32 in BF16 rounds to the nearest such value, ties to the one whose
+    # bit 16 is zero (IEEE round to nearest even).
+    cases = [
+        (0x3F808000, 0x3F800000),  # tie, kept bit 16 even -> round down
+        (0x3F818000, 0x3F820000),  # tie, bit 16 odd -> round up to even
+        (0x3F807FFF, 0x3F800000),  # just below a tie -> down
+        (0x3F808001, 0x3F810000),  # just above a tie -> up
+        (0x3F81FFFF, 0x3F820000),  # carries into the next bf16 value
+        (0xBF808000, 0xBF800000),  # negative tie, even -> toward zero
+        (0xBF818000, 0xBF820000),  # negative tie, odd -> away from zero
+        (0x00000000, 0x00000000),  # +0
+        (0x80000000, 0x80000000),  # -0 keeps its sign
+        (0x00008000, 0x00000000),  # subnormal tie, even -> 0
+        (0x00018000, 0x00020000),  # subnormal tie, odd -> up
+        (0x00007FFF, 0x00000000),  # tiny subnormal -> +0
+        (0x807FFFFF, 0x80800000),  # largest negative subnormal -> -min normal
+        (0x7F7FFFFF, 0x7F800000),  # largest finite rounds to +inf
+        (0x7F7F7FFF, 0x7F7F0000),  # largest finite bf16 stays
+        (0xFF7F8000, 0xFF800000),  # tie at the top, odd -> -inf
+        (0x7F800000, 0x7F800000),  # +inf
+        (0xFF800000, 0xFF800000),  # -inf
+    ]
+    x = _f32_bits([c[0] for c in cases])
+    got = _bits(oracle.round_bf16(x))
+    assert [hex(g) for g in got] == [hex(c[1]) for c in cases]
+
+
+def test_round_bf16_nan_stays_nan():
+    # a NaN whose payload sits only in the low 16 bits must not become inf
+    x = _f32_bits([0x7F800001, 0xFF800001, 0x7FC00000, 0x7F80FFFF])
+    got = oracle.round_bf16(x)
+    assert np.all(np.isnan(got))
+    assert np.all(_bits(got) & 0xFFFF == 0)
+
+
+def _round_bf16_by_definition(x):
+    # nearest of the two neighbouring BF16 values (exact differences in
+    # FP64); ties to the one with bit 16 clear; inf beyond the largest
+    u = _bits(x).astype(np.uint64)
+    lo = (u & 0xFFFF0000).astype(np.uint32)
+    hi = (lo.astype(np.uint64) + 0x10000).astype(np.uint32)
+    xl = lo.view(np.float32).astype(np.float64)
+    xh = hi.view(np.float32).astype(np.float64)
+    # past the largest BF16 the next value up is 2^128 (unbounded exponent),
+    # stored as inf: IEEE rounding overflows from the midpoint on
+    xh = np.where(np.isinf(xh), np.copysign(2.0 ** 128, xh), xh)
+    xv = np.asarray(x, np.float32).astype(np.float64)
+    dl, dh = np.abs(xv - xl), np.abs(xh - xv)
+    even_lo = ((lo >> 16) & 1) == 0
+    pick_lo = (dl < dh) | ((dl == dh) & even_lo)
+    return np.where(pick_lo, lo, hi).astype(np.uint32)  # hi of 2^128 is the inf pattern
+
+
+def test_round_bf16_dense_sweep_against_definition_and_torch():
+    # every 257th bit pattern (all exponents, signs and low-bit phases) plus
+    # every pattern of two full 16-bit low halves around ties
+    rng = np.random.default_rng(11)
+    u = np.arange(0, 1 << 32, 257, dtype=np.uint64).astype(np.uint32)
+    hi_words = rng.integers(0, 1 << 16, 2, dtype=np.uint64).astype(np.uint32) << 16
+    u = np.concatenate([u] + [w | np.arange(1 << 16, dtype=np.uint32) for w in hi_words])
+    x = u.view(np.float32)
+    fin = np.isfinite(x)
+    got = _bits(oracle.round_bf16(x))
+    # finite inputs: the definition (a result beyond the largest BF16 is inf)
+    want = _round_bf16_by_definition(x[fin])
+    assert np.array_equal(got[fin], want)
+    # and the library's BF16 conversion agrees on every input, NaN as NaN
+    torch = pytest.importorskip("torch")
+    t = torch.from_numpy(x.copy()).to(torch.bfloat16).to(torch.float32).numpy()
+    nan = np.isnan(x)
+    assert np.array_equal(_bits(t)[~nan], got[~nan])
+    assert np.all(np.isnan(got.view(np.float32)[nan]))

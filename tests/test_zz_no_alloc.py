@@ -1,13 +1,12 @@
 """The allocation-free search entry point (st_stack_search_noalloc).
 
-Callers that cannot allocate device memory when they search (inside a CUDA
-stream capture, or with device memory reserved up front by another allocator)
-use this entry point; its scratch is a fixed array inside the library.  It
-must give the same sorted candidates as the planned search, on consecutive
-calls that reuse the array.  This file is named to be collected after the
-other tests (only the long full-size parity test follows it), so a run that
-stops at the first failure has run them first; it also passes alone in a
-fresh process.
+Callers that cannot allocate device memory when they search (their device
+memory is reserved up front by another allocator, or their host forbids
+cudaMalloc after start-up) use this entry point; its scratch is a fixed
+array inside the library.  It must give the same sorted candidates as the
+planned search, on consecutive calls that reuse the array.  This file is
+named to be collected after every other test, so a run that stops at the
+first failure has run them first; it also passes alone in a fresh process.
 """
 import ctypes as C
 
