@@ -23,6 +23,7 @@ import time
 
 import numpy as np
 
+T_START = time.perf_counter()
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -83,6 +84,12 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=1,
+                    help="searches timed end to end through the host-buffer entry point")
+    ap.add_argument("--time-budget", type=float, default=1500.0,
+                    help="wall-clock seconds the whole run aims to stay within: warm-up "
+                         "steps beyond 3 and then timed steps are cut (and reported) when "
+                         "the measured step time would overrun it")
     ap.add_argument("--width", type=int, default=None,
                     help="override the workload's frame size (square), e.g. for a profiling case")
     ap.add_argument("--frames", type=int, default=None, help="override the frame count")
@@ -632,8 +639,32 @@ def main():
             raise RuntimeError(f"search status {status}")
         return n
 
-    for _ in range(args.warmup):
+    # warm-up (the first step autotunes); the wall-clock guard keeps the run
+    # inside --time-budget: it stops warming up after 3 steps, then cuts the
+    # timed steps, when the measured step time says the rest would not fit
+    steps_requested, warmup_requested = args.steps, args.warmup
+    t_w = 0.0
+    done_w = 0
+    for w_i in range(args.warmup):
+        t0 = time.perf_counter()
         n_found = step()
+        torch.cuda.synchronize()
+        t_w = time.perf_counter() - t0
+        done_w += 1
+        extra = (args.e2e_steps * 1.2 * t_w if not args.no_e2e else 0.0) + \
+            (args.cpu_seconds * 2 + 10 if not args.no_cpu_baseline else 0.0) + 30.0
+        left = args.time_budget - (time.perf_counter() - T_START)
+        if done_w >= 3 and (args.warmup - done_w + args.steps) * t_w + extra > left:
+            break
+    args.warmup = done_w
+    if t_w > 0:
+        left = args.time_budget - (time.perf_counter() - T_START) - extra
+        fit = int(left // (t_w * 1.02))
+        if world > 1:
+            tt = torch.tensor([fit], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MIN)
+            fit = int(tt.item())
+        args.steps = max(1, min(args.steps, fit))
     clocks = Clocks(local)
     if world > 1:
         torch.distributed.barrier()
@@ -683,10 +714,11 @@ def main():
 
         if world > 1:
             torch.distributed.barrier()
+        n_e2e = max(1, args.e2e_steps)
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(n_e2e):
             nh = host_step()
-        te = (time.perf_counter() - t0) / args.steps
+        te = (time.perf_counter() - t0) / n_e2e
         if world > 1:
             tt = torch.tensor([te], device=dev)
             torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
@@ -694,7 +726,7 @@ def main():
         e2e = {"value": job_adds / te / 1e9, "unit": "G adds/s",
                "h2d_bytes_per_step": int(sum(h.numel() * 4 for h in hframes) +
                                          sum(t_.nbytes for t_ in tarr)),
-               "d2h_bytes_per_step": int(nh * 28 + 32), "s_per_step": te}
+               "d2h_bytes_per_step": int(nh * 28 + 32), "s_per_step": te, "steps": n_e2e}
 
     if rank != 0:
         return
@@ -762,6 +794,10 @@ def main():
         "fields_per_hr": 3600.0 / t_step * (BATCH if batch_total is not None else world),
         "candidates": int(n_found), "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
         "e2e": e2e, "gpu_launches": int(launches), "device": props.name}
+    if (args.steps, args.warmup) != (steps_requested, warmup_requested):
+        line["time_guard"] = {"steps_requested": steps_requested,
+                              "warmup_requested": warmup_requested,
+                              "budget_s": args.time_budget, "warmup_step_s": t_w}
     if precision:
         line["precision"] = precision
     if tracks:
