@@ -25,12 +25,14 @@
 //   the 4 y-velocities: y-velocity j reads window row r + c_j for output row
 //   r.  The row offsets c_j form a monotone staircase with steps of 0 or 1
 //   (15 patterns); the pattern is the same for the whole block in a frame, so
-//   one switch per frame picks a straight-line body.  Nearest: even offsets
-//   use paired adds (add.f32x2) on row pairs, odd offsets scalar adds (the
-//   column-pair variant pairs the two columns instead, so every add is
-//   paired).  Bilinear: the warp's horizontal interpolation of each window
-//   row is formed once and shared by the 4 y-velocities, each adding
-//   (1 - fy) h[r + c_j] + fy h[r + c_j + 1] as two fused multiply-adds.
+//   one switch per frame picks a straight-line body.  Accumulators are held
+//   as row pairs (m, m + KY/2) and the window as pairs (q, q + KY/2), so
+//   output pair m of y-velocity j adds window pair m + c_j: every add is a
+//   paired add (add.f32x2) whatever the offsets' parity (the column-pair
+//   variant pairs the two columns instead).  Bilinear: the warp's horizontal
+//   interpolation of each window row is formed once and shared by the 4
+//   y-velocities, each adding (1 - fy) h[r + c_j] + fy h[r + c_j + 1] as two
+//   fused multiply-adds, paired the same way (fma.rn.f32x2).
 // * After the last frame, outputs are compared with the item's lowest
 //   possible threshold; the rare survivors go to the warp-aggregated pending
 //   list, where the resolver forms their exact value, coverage and local
@@ -51,6 +53,7 @@
 #include <new>
 #include <utility>
 
+#include "st_bodies.inc"
 #include "st_internal.h"
 #include "st_pending.cuh"
 #include "st_sample.cuh"
@@ -236,29 +239,41 @@ __global__ void k_cov_tables(const int32_t* __restrict__ sh, int N, int nv, int 
   for (int s = 1; s < span; ++s) row[s] += row[s - 1];
 }
 
-// acc[j][r] += window[r + C] for the KY rows of a thread, as KY/2 row pairs.
-template <int KY, int C, int M>
-__device__ __forceinline__ void add_rows(float2 (&acc)[KY / 2], const float (&w)[KY + 3]) {
-  if constexpr ((C & 1) == 0) {
-    acc[M] = __fadd2_rn(acc[M], make_float2(w[2 * M + C], w[2 * M + C + 1]));
-  } else {
-    acc[M].x = __fadd_rn(acc[M].x, w[2 * M + C]);
-    acc[M].y = __fadd_rn(acc[M].y, w[2 * M + C + 1]);
-  }
-}
-
-template <int KY, int C, int... M>
-__device__ __forceinline__ void add_column(float2 (&acc)[KY / 2], const float (&w)[KY + 3],
-                                           std::integer_sequence<int, M...>) {
-  (add_rows<KY, C, M>(acc, w), ...);
+// Row pairs: accumulator pair m of a y-velocity holds output rows m and
+// m + KY/2, and pair window q holds window rows (q, q + KY/2).  Output row r
+// of y-velocity j reads window row r + c_j, so pair m reads pair window
+// m + c_j for any offset c_j: every add is a paired add (add.f32x2) on an
+// aligned register pair, whatever the parity of the staircase offsets.
+template <int KY, int C>
+__device__ __forceinline__ void add_pair_column(float2 (&acc)[KY / 2],
+                                                const float2 (&pw)[KY / 2 + 3]) {
+#pragma unroll
+  for (int m = 0; m < KY / 2; ++m) acc[m] = __fadd2_rn(acc[m], pw[m + C]);
 }
 
 template <int KY, int ID>
-__device__ __forceinline__ void add_pattern(float2 (&acc)[kMB][KY / 2], const float (&w)[KY + 3]) {
-  add_column<KY, pat_off(ID, 0)>(acc[0], w, std::make_integer_sequence<int, KY / 2>{});
-  add_column<KY, pat_off(ID, 1)>(acc[1], w, std::make_integer_sequence<int, KY / 2>{});
-  add_column<KY, pat_off(ID, 2)>(acc[2], w, std::make_integer_sequence<int, KY / 2>{});
-  add_column<KY, pat_off(ID, 3)>(acc[3], w, std::make_integer_sequence<int, KY / 2>{});
+__device__ __forceinline__ void add_pattern(float2 (&acc)[kMB][KY / 2],
+                                            const float2 (&pw)[KY / 2 + 3]) {
+  add_pair_column<KY, pat_off(ID, 0)>(acc[0], pw);
+  add_pair_column<KY, pat_off(ID, 1)>(acc[1], pw);
+  add_pair_column<KY, pat_off(ID, 2)>(acc[2], pw);
+  add_pair_column<KY, pat_off(ID, 3)>(acc[3], pw);
+}
+
+// The body of pattern id in [B, B + 2^L) by L levels of branches on the bits
+// of id (uniform across the block: every warp sees the same id); id kPatterns
+// is a padding frame (no adds).
+template <int KY, int L, int B>
+__device__ __forceinline__ void dispatch_tree(int id, float2 (&acc)[kMB][KY / 2],
+                                              const float2 (&pw)[KY / 2 + 3]) {
+  if constexpr (L == 0) {
+    if constexpr (B < kPatterns) add_pattern<KY, B>(acc, pw);
+  } else {
+    if (id & (1 << (L - 1)))
+      dispatch_tree<KY, L - 1, B + (1 << (L - 1))>(id, acc, pw);
+    else
+      dispatch_tree<KY, L - 1, B>(id, acc, pw);
+  }
 }
 
 // Column pairs: the thread's two columns (c and c + 32) share every row
@@ -276,28 +291,28 @@ __device__ __forceinline__ void add_pattern_cp(float2 (&acc)[kMB][KY], const flo
 // the horizontal interpolation h[r] = c0[r] + fx (c1[r] - c0[r]) of window row
 // r is formed once per frame and shared; y-velocity j then adds
 // (1 - fy_j) h[r + c_j] + fy_j h[r + c_j + 1] to output row r as two fused
-// multiply-adds.  (The generic kernel forms the same bilinear sample as four
-// weighted taps; the two agree to FP32 rounding, and the local-maximum
-// resolver re-forms every reported value with the generic arithmetic.)
+// multiply-adds, on row pairs (m, m + KY/2) as paired FMAs (fma.rn.f32x2)
+// with the pair window hp[q] = (h[q], h[q + KY/2]).  (The generic kernel
+// forms the same bilinear sample as four weighted taps; the two agree to
+// FP32 rounding, and the local-maximum resolver re-forms every reported
+// value with the generic arithmetic.)
 template <int KY, int C>
 __device__ __forceinline__ void add_bl_column(float2 (&acc)[KY / 2], float gy, float fy,
-                                              const float (&h)[KY + 4]) {
+                                              const float2 (&hp)[KY / 2 + 4]) {
+  const float2 g2 = make_float2(gy, gy), f2 = make_float2(fy, fy);
 #pragma unroll
-  for (int m = 0; m < KY / 2; ++m) {
-    const int r = 2 * m + C;
-    acc[m].x = __fmaf_rn(fy, h[r + 1], __fmaf_rn(gy, h[r], acc[m].x));
-    acc[m].y = __fmaf_rn(fy, h[r + 2], __fmaf_rn(gy, h[r + 1], acc[m].y));
-  }
+  for (int m = 0; m < KY / 2; ++m)
+    acc[m] = __ffma2_rn(f2, hp[m + C + 1], __ffma2_rn(g2, hp[m + C], acc[m]));
 }
 
 template <int KY, int ID>
 __device__ __forceinline__ void add_pattern_bl(float2 (&acc)[kMB][KY / 2], const float (&gy)[kMB],
                                                const float (&fy)[kMB],
-                                               const float (&h)[KY + 4]) {
-  add_bl_column<KY, pat_off(ID, 0)>(acc[0], gy[0], fy[0], h);
-  add_bl_column<KY, pat_off(ID, 1)>(acc[1], gy[1], fy[1], h);
-  add_bl_column<KY, pat_off(ID, 2)>(acc[2], gy[2], fy[2], h);
-  add_bl_column<KY, pat_off(ID, 3)>(acc[3], gy[3], fy[3], h);
+                                               const float2 (&hp)[KY / 2 + 4]) {
+  add_bl_column<KY, pat_off(ID, 0)>(acc[0], gy[0], fy[0], hp);
+  add_bl_column<KY, pat_off(ID, 1)>(acc[1], gy[1], fy[1], hp);
+  add_bl_column<KY, pat_off(ID, 2)>(acc[2], gy[2], fy[2], hp);
+  add_bl_column<KY, pat_off(ID, 3)>(acc[3], gy[3], fy[3], hp);
 }
 
 // Number of frames whose shift s satisfies lo <= s <= hi, from a prefix table.
@@ -338,17 +353,21 @@ struct Item {
   int X0, Y0, A, B;
 };
 // Items of a field for tile height ky and width tx: super-tiles x 16 tiles x
-// velocity tiles.
+// velocity tiles; an item of a CTA with h halves covers h x-velocity tiles
+// (item A indexes groups of h tiles).
 __device__ __host__ __forceinline__ int super_x_of(int W, int tx) {
   return ((W + tx - 1) / tx + kSuper - 1) / kSuper;
 }
-__device__ __host__ __forceinline__ int64_t items_of(const FastField& ff, int ky, int tx) {
+__device__ __host__ __forceinline__ int groups_of(int nA, int h) { return (nA + h - 1) / h; }
+__device__ __host__ __forceinline__ int64_t items_of(const FastField& ff, int ky, int tx,
+                                                     int h) {
   const int sy = ((ff.H + ky - 1) / ky + kSuper - 1) / kSuper;
-  return (int64_t)super_x_of(ff.W, tx) * sy * kSuper * kSuper * ff.nA * ff.nB;
+  return (int64_t)super_x_of(ff.W, tx) * sy * kSuper * kSuper * groups_of(ff.nA, h) * ff.nB;
 }
 __device__ __forceinline__ Item decode_item(const FastField& ff, int f, int64_t L, int ky,
-                                            int tx) {
-  const int nVT = ff.nA * ff.nB;
+                                            int tx, int h) {
+  const int nAg = groups_of(ff.nA, h);
+  const int nVT = nAg * ff.nB;
   const int super_x = super_x_of(ff.W, tx);
   const int sub = (int)(L % (kSuper * kSuper));
   const int64_t rest = L / (kSuper * kSuper);
@@ -358,8 +377,8 @@ __device__ __forceinline__ Item decode_item(const FastField& ff, int f, int64_t 
   it.f = f;
   it.X0 = ((stile % super_x) * kSuper + sub % kSuper) * tx;
   it.Y0 = ((stile / super_x) * kSuper + sub / kSuper) * ky;
-  it.A = vt % ff.nA;
-  it.B = vt / ff.nA;
+  it.A = vt % nAg;
+  it.B = vt / nAg;
   return it;
 }
 
@@ -381,17 +400,23 @@ __device__ __forceinline__ void tmap_acquire(const CUtensorMap* m) {
 // item's count of fully-inside frames in shared memory.  Warps 0..7 consume.
 // A ring of S stages runs continuously across items and fields; when the
 // work runs out the producer publishes an end item.  Every wait is bounded.
-template <typename T, int KY, int S, int F, bool DUMP, bool BL, bool CP>
-__global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
-    k_stack_fast(const __grid_constant__ FastArgs p) {
+// OPT (nearest sampling): bit 0 dispatches the frame's pattern by a binary
+// tree of uniform branches on its bits instead of a switch; bit 1 unrolls the
+// frames of a stage.
+// H: halves per CTA.  With H = 2 the CTA has 16 consumer warps and one
+// producer (one CTA per SM, 112 registers a thread): an item covers two
+// x-velocity tiles, each with its own box per frame and its own 8 warps.
+template <typename T, int KY, int S, int F, bool DUMP, bool BL, bool CP, int OPT, int H>
+__device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
   static_assert(!(CP && BL), "column pairs are built for nearest sampling");
+  static_assert(H == 1 || !(CP || BL), "two halves are built for single-column nearest sampling");
   constexpr int kTXv = CP ? 2 * kTX : kTX;  // tile width: one or two columns per lane
   constexpr int kBoxW = Store<T>::kBoxW + (CP ? kTX : 0);
   constexpr int kAccN = CP ? KY : KY / 2;   // paired accumulators per y-velocity
   constexpr int kTY = KY;         // tile height: one row group of KY rows per thread
   constexpr int kBoxH = KY + 3 + (BL ? 1 : 0);  // tile rows + staircase offset (+ lower tap)
   constexpr int kEdge = BL ? 1 : 0;  // a bilinear sample also reads the next column / row
-  constexpr int kCW = kXV;        // consumer warps
+  constexpr int kCW = kXV * H;    // consumer warps
   constexpr int kOut = kMB * KY * (CP ? 2 : 1);  // outputs per thread per item
   constexpr int kItemSlots = 8;
   constexpr int kNoop = kPatterns;  // pattern id of a padding frame
@@ -399,11 +424,17 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
   extern __shared__ __align__(128) float smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[S];
   __shared__ __align__(8) uint64_t empty_bar[S];
-  __shared__ __align__(16) uint32_t slot_ocol[S * F];  // packed 4-bit column offsets of the 8 warps
+  __shared__ __align__(16) uint32_t slot_ocol[S * H * F];  // packed 4-bit column offsets of 8 warps
   __shared__ uint32_t slot_ids[S];          // packed 8-bit pattern ids of the stage's frames
+  // OPT bit 3 (lean stage loop): per stage, warp and frame, the byte offset of
+  // the warp's window in the ring with the pattern id in the top byte
+  constexpr bool kLean = (OPT & 24) != 0;
+  // OPT bit 4: the whole item's stages (waits, frames, releases) in one PTX block
+  constexpr bool kItemPtx = (OPT & 16) != 0;
+  __shared__ __align__(16) uint32_t slot_word[kLean ? S * kCW * F : 1];
   __shared__ float slot_fx[BL ? S * F * kXV : 1];  // bilinear: x-fraction of each warp
   __shared__ float4 slot_fy[BL ? S * F : 1];       // bilinear: y-fractions of the 4 y-velocities
-  __shared__ int item_inside[kItemSlots];   // frames of an item fully inside the frame
+  __shared__ int item_inside[kItemSlots * H];  // frames of an item half fully inside the frame
   __shared__ int item_done[kItemSlots];     // consumer warps done with an item
   __shared__ Item item_info[kItemSlots];    // the items in flight
 
@@ -421,89 +452,152 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
     }
     mbar_init_fence();
   }
-  if (tid < kItemSlots) {
-    item_inside[tid] = 0;
-    item_done[tid] = 0;
-  }
+  if (tid < kItemSlots * H) item_inside[tid] = 0;
+  if (tid < kItemSlots) item_done[tid] = 0;
   __syncthreads();
 
-  if (warp == kXV) {
+  if (warp == kCW) {
     // ------------------------------------------------------------ producer
-    int slot = 0, f = 0, acq_f = -1;
-    int64_t base = 0;                        // first item of field f
-    int64_t f_items = items_of(*p.ff[0], KY, kTXv);  // items of field f
-    int64_t seq = 0;  // stages issued
-    bool ok = true;
-    for (int item = 0; ok; ++item) {
+    // Lane l < H*F handles frame l % F of a stage for half l / F.  The table
+    // entries of the next stage are loaded while the current one waits for
+    // its ring slot, and the next item's index is taken from the work counter
+    // one item ahead, so neither global-memory latency sits between a free
+    // slot and its copies.
+    constexpr int kLanes = H * F;
+    const int fi_l = lane % F, h_l = lane / F;
+    int f = 0, acq_f = -1;
+    int64_t base = 0;                                  // first item of field f
+    int64_t f_items = items_of(*p.ff[0], KY, kTXv, H);  // items of field f
+    // the item of work-counter index L (-1: past the end); L only grows
+    auto locate = [&](int64_t L) -> Item {
+      Item it{-1, 0, 0, 0, 0};
+      if (L >= p.n_items) return it;
+      while (L >= base + f_items) {
+        base += f_items;
+        f_items = items_of(*p.ff[++f], KY, kTXv, H);
+      }
+      return decode_item(*p.ff[f], f, L - base, KY, kTXv, H);
+    };
+    auto take = [&]() -> int64_t {
       int64_t L = 0;
       if (lane == 0) L = (int64_t)atomicAdd(p.work, 1ull);
-      L = __shfl_sync(0xffffffffu, L, 0);
-      const bool done = L >= p.n_items;
-      // the field of item L (items are taken in increasing order)
-      while (!done && L >= base + f_items) {
-        base += f_items;
-        f_items = items_of(*p.ff[++f], KY, kTXv);
+      return __shfl_sync(0xffffffffu, L, 0);
+    };
+    // per-stage table entries of this lane's frame (valid: a real copy)
+    struct Entry {
+      int4 xe, ye;
+      unsigned id;
+      bool valid;
+      float4 f0, f1, fy;
+    };
+    auto load_entry = [&](const Item& it, int st) -> Entry {
+      Entry e{};
+      e.id = kNoop;
+      e.valid = false;
+      if (it.f < 0 || lane >= kLanes) return e;
+      const FastField& ff = *p.ff[it.f];
+      const int fr = st * F + fi_l;
+      const int A = it.A * H + h_l;
+      if (fr >= ff.N) return e;
+      e.ye = __ldg(ff.yt + (int64_t)fr * ff.nB + it.B);
+      e.id = ff.pat[(int64_t)fr * ff.nB + it.B];
+      if (A >= ff.nA) return e;  // the second half of a field's last tile group
+      e.xe = __ldg(ff.xt + (int64_t)fr * ff.nA + A);
+      e.valid = true;
+      if constexpr (BL) {
+        e.f0 = __ldg(ff.fxt + 2 * ((int64_t)fr * ff.nA + A));
+        e.f1 = __ldg(ff.fxt + 2 * ((int64_t)fr * ff.nA + A) + 1);
+        e.fy = __ldg(ff.fyt + (int64_t)fr * ff.nB + it.B);
       }
-      const FastField& ff = *p.ff[f];
-      Item it{-1, 0, 0, 0, 0};
-      if (!done) it = decode_item(ff, f, L - base, KY, kTXv);
-      const CUtensorMap* map = p.maps[f];
-      if (!done && f != acq_f) {
+      return e;
+    };
+    int slot = 0;
+    int64_t seq = 0;  // stages issued
+    bool ok = true;
+    Item it = locate(take());
+    int64_t L_next = it.f >= 0 ? take() : p.n_items;
+    int st = 0;
+    Entry cur = load_entry(it, 0);
+    for (int item = 0; ok;) {
+      const bool done = it.f < 0;
+      const int N = done ? 1 : p.ff[it.f]->N;
+      const int spi = (N + F - 1) / F;  // stages of this item (an end item: one)
+      const CUtensorMap* map = done ? nullptr : p.maps[it.f];
+      if (!done && it.f != acq_f) {
         if (lane == 0) {
           tmap_acquire(map);
           tma_prefetch_desc(map);
         }
-        acq_f = f;
+        acq_f = it.f;
       }
-      const int N = done ? 1 : ff.N;
-      const int spi = (N + F - 1) / F;  // stages of this item (an end item: one)
-      for (int st = 0; st < spi; ++st, ++seq) {
-        if (seq >= S &&
-            !mbar_wait_sleep(&empty_bar[slot], (uint32_t)(seq / S - 1) & 1u, kWaitNs,
-                             kProducerSleepNs)) {
-          if (lane == 0) atomicOr(&p.ctr->error, ERR_TIMEOUT);
-          ok = false;
-          break;  // consumers time out on the missing stage (bounded)
-        }
-        if (st == 0 && lane == 0) item_info[item % kItemSlots] = it;
-        const int nbox = done ? 0 : min(F, N - st * F);  // real frames in this stage
-        if (lane == 0 && nbox > 0) mbar_expect_tx(&full_bar[slot], box_bytes * (uint32_t)nbox);
-        unsigned id = kNoop;  // padding frames (and bytes past F) are no-ops
-        {
-          if (lane < nbox) {
-            const int fr = st * F + lane;
-            const int4 xe = __ldg(ff.xt + (int64_t)fr * ff.nA + it.A);
-            const int4 ye = __ldg(ff.yt + (int64_t)fr * ff.nB + it.B);
-            id = ff.pat[(int64_t)fr * ff.nB + it.B];
-            slot_ocol[slot * F + lane] = (uint32_t)xe.y;
-            if constexpr (BL) {
-              const float4 f0 = __ldg(ff.fxt + 2 * ((int64_t)fr * ff.nA + it.A));
-              const float4 f1 = __ldg(ff.fxt + 2 * ((int64_t)fr * ff.nA + it.A) + 1);
-              float* d = slot_fx + (slot * F + lane) * kXV;
-              d[0] = f0.x; d[1] = f0.y; d[2] = f0.z; d[3] = f0.w;
-              d[4] = f1.x; d[5] = f1.y; d[6] = f1.z; d[7] = f1.w;
-              slot_fy[slot * F + lane] = __ldg(ff.fyt + (int64_t)fr * ff.nB + it.B);
-            }
-            // every sample of the item strictly inside (bilinear: with its
-            // right and lower taps), so every output of the item is covered
-            const bool inside = it.X0 + xe.z >= 0 && it.X0 + kTXv - 1 + xe.w + kEdge < ff.W &&
-                                it.Y0 + ye.x >= 0 && it.Y0 + kTY - 1 + ye.y + kEdge < ff.H;
-            if (inside) atomicAdd(&item_inside[item % kItemSlots], 1);
-            tma_load_3d(smem + (size_t)(slot * F + lane) * box_floats, map, it.X0 + xe.x,
-                        it.Y0 + ye.x, fr, &full_bar[slot]);
+      // the next stage: of this item, or the first of the next item
+      Item it_n = it;
+      int st_n = st + 1;
+      if (st_n == spi) {
+        it_n = done ? it : locate(L_next);
+        st_n = 0;
+      }
+      const Entry nxt = done ? cur : load_entry(it_n, st_n);
+      if (seq >= S &&
+          !mbar_wait_sleep(&empty_bar[slot], (uint32_t)(seq / S - 1) & 1u, kWaitNs,
+                           kProducerSleepNs)) {
+        if (lane == 0) atomicOr(&p.ctr->error, ERR_TIMEOUT);
+        ok = false;
+        break;  // consumers time out on the missing stage (bounded)
+      }
+      if (st == 0 && lane == 0) item_info[item % kItemSlots] = it;
+      const unsigned copies = __ballot_sync(0xffffffffu, cur.valid);
+      if (lane == 0 && copies) mbar_expect_tx(&full_bar[slot], box_bytes * __popc(copies));
+      if constexpr (kLean) {
+        if (lane < kLanes) {
+          const uint32_t base =
+              (uint32_t)(((slot * F + fi_l) * H + h_l) * box_floats * (int)sizeof(T));
+          const uint32_t idb = (cur.valid ? cur.id : (unsigned)kNoop) << 24;
+#pragma unroll
+          for (int w = 0; w < kXV; ++w) {
+            const uint32_t oc = cur.valid ? ((uint32_t)cur.xe.y >> (4 * w)) & 15u : 0u;
+            slot_word[(slot * kCW + h_l * kXV + w) * F + fi_l] =
+                (base + oc * (uint32_t)sizeof(T)) | idb;
           }
         }
-        // the stage's ids, packed: lane l's id in byte l
-        uint32_t w = lane < 4 ? id << (8 * lane) : 0u;
-        w |= __shfl_xor_sync(0xffffffffu, w, 1);
-        w |= __shfl_xor_sync(0xffffffffu, w, 2);
-        if (lane == 0) slot_ids[slot] = w;
-        __threadfence_block();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&full_bar[slot]);  // releases this stage's info
-        if (++slot == S) slot = 0;
       }
+      if (cur.valid) {
+        const FastField& ff = *p.ff[it.f];
+        const int fr = st * F + fi_l;
+        slot_ocol[(slot * H + h_l) * F + fi_l] = (uint32_t)cur.xe.y;
+        if constexpr (BL) {
+          float* d = slot_fx + (slot * F + fi_l) * kXV;
+          d[0] = cur.f0.x; d[1] = cur.f0.y; d[2] = cur.f0.z; d[3] = cur.f0.w;
+          d[4] = cur.f1.x; d[5] = cur.f1.y; d[6] = cur.f1.z; d[7] = cur.f1.w;
+          slot_fy[slot * F + fi_l] = cur.fy;
+        }
+        // every sample of the half strictly inside (bilinear: with its right
+        // and lower taps), so every output of the half is covered
+        const bool inside = it.X0 + cur.xe.z >= 0 &&
+                            it.X0 + kTXv - 1 + cur.xe.w + kEdge < ff.W &&
+                            it.Y0 + cur.ye.x >= 0 && it.Y0 + kTY - 1 + cur.ye.y + kEdge < ff.H;
+        if (inside) atomicAdd(&item_inside[(item % kItemSlots) * H + h_l], 1);
+        tma_load_3d(smem + (size_t)((slot * F + fi_l) * H + h_l) * box_floats, map,
+                    it.X0 + cur.xe.x, it.Y0 + cur.ye.x, fr, &full_bar[slot]);
+      }
+      // the stage's ids (the same for both halves), packed: frame fi in byte fi
+      uint32_t w = lane < F ? cur.id << (8 * lane) : 0u;
+      w |= __shfl_xor_sync(0xffffffffu, w, 1);
+      w |= __shfl_xor_sync(0xffffffffu, w, 2);
+      if (lane == 0) slot_ids[slot] = w;
+      __threadfence_block();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&full_bar[slot]);  // releases this stage's info
+      if (++slot == S) slot = 0;
+      ++seq;
       if (done) break;
+      if (st_n == 0) {  // next item: take the one after it from the counter
+        ++item;
+        it = it_n;
+        L_next = it.f >= 0 ? take() : p.n_items;
+      }
+      st = st_n;
+      cur = nxt;
     }
     // drain (matters only after a consumer timeout): the last use of each
     // ring slot completes before the CTA may exit.  Only the latest phase of a
@@ -516,7 +610,7 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
   }
 
   // -------------------------------------------------------------- consumers
-  const int xw = warp;
+  const int xw = warp % kXV, hw = warp / kXV;  // x-velocity in the half, half
   int c_slot = 0;
   uint32_t c_ph = 0;
   for (int item = 0;; ++item) {
@@ -535,32 +629,73 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
     for (int j = 0; j < kMB; ++j)
 #pragma unroll
       for (int m = 0; m < kAccN; ++m) acc[j][m] = make_float2(0.0f, 0.0f);
+    // OPT bit 2: the accumulators as 64-bit register pairs for the PTX bodies
+    constexpr bool kPtx = (OPT & 4) != 0;
+    constexpr bool kAcc64 = kPtx || kLean;
+    unsigned long long acc64[kAcc64 ? kMB * kAccN : 1];
+#pragma unroll
+    for (int a = 0; a < (kAcc64 ? kMB * kAccN : 1); ++a) acc64[a] = 0ull;
 
     bool ok = true;
-    for (int st = 0; st < spi; ++st) {
+    if constexpr (kItemPtx) {
+      static_assert(KY == 16 && F == 4 && kCW == 8 && sizeof(T) == 4 && (S == 8 || S == 6),
+                    "the item loop is generated for FP32, KY = 16, F = 4, 8 warps, S = 6 or 8");
+      uint32_t slot = (uint32_t)c_slot, ph = c_ph, err = 0;
+      const uint32_t wb0 = smem_u32(&slot_word[warp * F]);
+      const uint32_t lb = smem_u32(smem) + lane * (uint32_t)sizeof(T);
+      const uint32_t fb0 = smem_u32(&full_bar[0]), eb0 = smem_u32(&empty_bar[0]);
+      const uint32_t nst = (uint32_t)spi, skip = 1u;
+      if constexpr (S == 8)
+        asm volatile(ST_ITEM_KY16_F4_R160_S8_W8
+                     ST_ITEM_OPERANDS_KY16(acc64, slot, ph, err, nst, skip, wb0, lb, fb0, eb0));
+      else
+        asm volatile(ST_ITEM_KY16_F4_R160_S6_W8
+                     ST_ITEM_OPERANDS_KY16(acc64, slot, ph, err, nst, skip, wb0, lb, fb0, eb0));
+      c_slot = (int)slot;
+      c_ph = ph;
+      if (err) {
+        if (lane == 0) atomicOr(&p.ctr->error, ERR_TIMEOUT);
+        ok = false;
+      }
+    }
+    for (int st = 0; st < (kItemPtx ? 0 : spi); ++st) {
       if (st > 0 && !__all_sync(0xffffffffu, mbar_wait(&full_bar[c_slot], c_ph, kWaitNs))) {
         if (lane == 0) atomicOr(&p.ctr->error, ERR_TIMEOUT);
         ok = false;
         break;
       }
+      if constexpr (kLean) {
+        static_assert(KY == 16 && F == 4 && !CP && !BL && sizeof(T) == 4,
+                      "the lean stage loop is generated for FP32, KY = 16, F = 4");
+        const uint32_t wb = smem_u32(&slot_word[(c_slot * kCW + warp) * F]);
+        const uint32_t lb = smem_u32(smem) + lane * (uint32_t)sizeof(T);
+        asm volatile(ST_STAGE_KY16_F4_R160 ST_STAGE_OPERANDS_KY16(acc64, wb, lb));
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty_bar[c_slot]);
+        if (++c_slot == S) {
+          c_slot = 0;
+          c_ph ^= 1u;
+        }
+        continue;
+      }
       const uint32_t idw = slot_ids[c_slot];  // the stage's pattern ids
-      const T* stage = smem + (size_t)(c_slot * F) * box_floats + lane;
+      const T* stage = smem + (size_t)(c_slot * F * H + hw) * box_floats + lane;
       // this warp's column offsets of the stage's frames, 4 bits each, from
       // one vector load of the stage's packed words
       uint32_t ocw = 0;
       if constexpr (F == 4) {
-        const uint4 q = *reinterpret_cast<const uint4*>(slot_ocol + c_slot * F);
+        const uint4 q = *reinterpret_cast<const uint4*>(slot_ocol + (c_slot * H + hw) * F);
         ocw = ((q.x >> (4 * xw)) & 15u) | (((q.y >> (4 * xw)) & 15u) << 4) |
               (((q.z >> (4 * xw)) & 15u) << 8) | (((q.w >> (4 * xw)) & 15u) << 12);
       } else {
 #pragma unroll
         for (int fi = 0; fi < F; ++fi)
-          ocw |= ((slot_ocol[c_slot * F + fi] >> (4 * xw)) & 15u) << (4 * fi);
+          ocw |= ((slot_ocol[(c_slot * H + hw) * F + fi] >> (4 * xw)) & 15u) << (4 * fi);
       }
-#pragma unroll 1
+#pragma unroll((OPT & 2) ? F : 1)
       for (int fi = 0; fi < F; ++fi) {
         const int id = (idw >> (8 * fi)) & 0xffu;
-        const T* col = stage + fi * box_floats + ((ocw >> (4 * fi)) & 15u);
+        const T* col = stage + fi * H * box_floats + ((ocw >> (4 * fi)) & 15u);
         if constexpr (BL) {
           float h[KY + 4];
           const float fxw = slot_fx[(c_slot * F + fi) * kXV + xw];
@@ -569,6 +704,9 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
             const float a0 = Store<T>::f(col[r * kBoxW]), a1 = Store<T>::f(col[r * kBoxW + 1]);
             h[r] = __fmaf_rn(fxw, __fsub_rn(a1, a0), a0);
           }
+          float2 hp[KY / 2 + 4];
+#pragma unroll
+          for (int q = 0; q < KY / 2 + 4; ++q) hp[q] = make_float2(h[q], h[q + KY / 2]);
           const float4 fy4 = slot_fy[c_slot * F + fi];
           if (fi == F - 1) {
             __syncwarp();
@@ -578,21 +716,21 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
           const float gy[kMB] = {__fsub_rn(1.0f, fy4.x), __fsub_rn(1.0f, fy4.y),
                                  __fsub_rn(1.0f, fy4.z), __fsub_rn(1.0f, fy4.w)};
           switch (id) {
-            case 0: add_pattern_bl<KY, 0>(acc, gy, fy, h); break;
-            case 1: add_pattern_bl<KY, 1>(acc, gy, fy, h); break;
-            case 2: add_pattern_bl<KY, 2>(acc, gy, fy, h); break;
-            case 3: add_pattern_bl<KY, 3>(acc, gy, fy, h); break;
-            case 4: add_pattern_bl<KY, 4>(acc, gy, fy, h); break;
-            case 5: add_pattern_bl<KY, 5>(acc, gy, fy, h); break;
-            case 6: add_pattern_bl<KY, 6>(acc, gy, fy, h); break;
-            case 7: add_pattern_bl<KY, 7>(acc, gy, fy, h); break;
-            case 8: add_pattern_bl<KY, 8>(acc, gy, fy, h); break;
-            case 9: add_pattern_bl<KY, 9>(acc, gy, fy, h); break;
-            case 10: add_pattern_bl<KY, 10>(acc, gy, fy, h); break;
-            case 11: add_pattern_bl<KY, 11>(acc, gy, fy, h); break;
-            case 12: add_pattern_bl<KY, 12>(acc, gy, fy, h); break;
-            case 13: add_pattern_bl<KY, 13>(acc, gy, fy, h); break;
-            case 14: add_pattern_bl<KY, 14>(acc, gy, fy, h); break;
+            case 0: add_pattern_bl<KY, 0>(acc, gy, fy, hp); break;
+            case 1: add_pattern_bl<KY, 1>(acc, gy, fy, hp); break;
+            case 2: add_pattern_bl<KY, 2>(acc, gy, fy, hp); break;
+            case 3: add_pattern_bl<KY, 3>(acc, gy, fy, hp); break;
+            case 4: add_pattern_bl<KY, 4>(acc, gy, fy, hp); break;
+            case 5: add_pattern_bl<KY, 5>(acc, gy, fy, hp); break;
+            case 6: add_pattern_bl<KY, 6>(acc, gy, fy, hp); break;
+            case 7: add_pattern_bl<KY, 7>(acc, gy, fy, hp); break;
+            case 8: add_pattern_bl<KY, 8>(acc, gy, fy, hp); break;
+            case 9: add_pattern_bl<KY, 9>(acc, gy, fy, hp); break;
+            case 10: add_pattern_bl<KY, 10>(acc, gy, fy, hp); break;
+            case 11: add_pattern_bl<KY, 11>(acc, gy, fy, hp); break;
+            case 12: add_pattern_bl<KY, 12>(acc, gy, fy, hp); break;
+            case 13: add_pattern_bl<KY, 13>(acc, gy, fy, hp); break;
+            case 14: add_pattern_bl<KY, 14>(acc, gy, fy, hp); break;
             case kNoop: break;  // padding frame
             default: __builtin_unreachable();
           }
@@ -628,26 +766,39 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
           float w[KY + 3];
 #pragma unroll
           for (int r = 0; r < KY + 3; ++r) w[r] = Store<T>::f(col[r * kBoxW]);
+          float2 pw[KY / 2 + 3];  // (row q, row q + KY/2) of the window
+#pragma unroll
+          for (int q = 0; q < KY / 2 + 3; ++q) pw[q] = make_float2(w[q], w[q + KY / 2]);
           if (fi == F - 1) {
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty_bar[c_slot]);
           }
-          switch (id) {
-            case 0: add_pattern<KY, 0>(acc, w); break;
-            case 1: add_pattern<KY, 1>(acc, w); break;
-            case 2: add_pattern<KY, 2>(acc, w); break;
-            case 3: add_pattern<KY, 3>(acc, w); break;
-            case 4: add_pattern<KY, 4>(acc, w); break;
-            case 5: add_pattern<KY, 5>(acc, w); break;
-            case 6: add_pattern<KY, 6>(acc, w); break;
-            case 7: add_pattern<KY, 7>(acc, w); break;
-            case 8: add_pattern<KY, 8>(acc, w); break;
-            case 9: add_pattern<KY, 9>(acc, w); break;
-            case 10: add_pattern<KY, 10>(acc, w); break;
-            case 11: add_pattern<KY, 11>(acc, w); break;
-            case 12: add_pattern<KY, 12>(acc, w); break;
-            case 13: add_pattern<KY, 13>(acc, w); break;
-            case 14: add_pattern<KY, 14>(acc, w); break;
+          if constexpr (kPtx) {
+            static_assert(KY == 16 && !CP && !BL, "PTX bodies are generated for KY = 16");
+            unsigned long long pw64[KY / 2 + 3];
+#pragma unroll
+            for (int q = 0; q < KY / 2 + 3; ++q)
+              asm("mov.b64 %0, {%1, %2};" : "=l"(pw64[q]) : "f"(pw[q].x), "f"(pw[q].y));
+            const unsigned idu = (unsigned)id & 15u;
+            asm(ST_BODY_KY16 ST_BODY_OPERANDS_KY16(acc64, pw64, idu));
+          } else if constexpr ((OPT & 1) != 0) {
+            dispatch_tree<KY, 4, 0>(id, acc, pw);
+          } else switch (id) {
+            case 0: add_pattern<KY, 0>(acc, pw); break;
+            case 1: add_pattern<KY, 1>(acc, pw); break;
+            case 2: add_pattern<KY, 2>(acc, pw); break;
+            case 3: add_pattern<KY, 3>(acc, pw); break;
+            case 4: add_pattern<KY, 4>(acc, pw); break;
+            case 5: add_pattern<KY, 5>(acc, pw); break;
+            case 6: add_pattern<KY, 6>(acc, pw); break;
+            case 7: add_pattern<KY, 7>(acc, pw); break;
+            case 8: add_pattern<KY, 8>(acc, pw); break;
+            case 9: add_pattern<KY, 9>(acc, pw); break;
+            case 10: add_pattern<KY, 10>(acc, pw); break;
+            case 11: add_pattern<KY, 11>(acc, pw); break;
+            case 12: add_pattern<KY, 12>(acc, pw); break;
+            case 13: add_pattern<KY, 13>(acc, pw); break;
+            case 14: add_pattern<KY, 14>(acc, pw); break;
             case kNoop: break;  // padding frame
             default: __builtin_unreachable();
           }
@@ -659,12 +810,20 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
       }
     }
     if (!ok) break;
+    if constexpr (kAcc64) {
+#pragma unroll
+      for (int j = 0; j < kMB; ++j)
+#pragma unroll
+        for (int m = 0; m < kAccN; ++m)
+          asm("mov.b64 {%0, %1}, %2;" : "=f"(acc[j][m].x), "=f"(acc[j][m].y)
+              : "l"(acc64[j * kAccN + m]));
+    }
 
     // ---- epilogue of the item (its last stage was waited on, so the
     // producer's count is visible)
-    const int n_full = item_inside[item % kItemSlots];
+    const int n_full = item_inside[(item % kItemSlots) * H + hw];
     const int x = it.X0 + lane;
-    const int av = it.A * kXV + xw;
+    const int av = (it.A * H + hw) * kXV + xw;
     if constexpr (CP) {
       // outputs (j, r, h): y-velocity j, row r, column x + 32 h; value
       // acc[j][r].x (h = 0) or .y (h = 1); bit o = (j KY + r) 2 + h
@@ -749,7 +908,7 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
           for (int m = 0; m < KY / 2; ++m)
   #pragma unroll
             for (int h = 0; h < 2; ++h) {
-              const int bv = it.B * kMB + j, y = it.Y0 + 2 * m + h;
+              const int bv = it.B * kMB + j, y = it.Y0 + m + h * (KY / 2);
               if (x < ff.W && y < ff.H && av < ff.nvx && bv < ff.nvy) {
                 const int64_t o =
                     ((int64_t)bv * ff.nvx + av) * ff.W * (int64_t)ff.H + (int64_t)y * ff.W + x;
@@ -781,9 +940,9 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
           for (int j = 0; j < kMB; ++j)
   #pragma unroll
             for (int m = 0; m < KY / 2; ++m) {
-              const int o = j * KY + 2 * m;
-              mask[o / 32] |= (uint32_t)(acc[j][m].x >= thr_n) << (o % 32);
-              mask[o / 32] |= (uint32_t)(acc[j][m].y >= thr_n) << (o % 32 + 1);
+              const int o0 = j * KY + m, o1 = o0 + KY / 2;  // rows m and m + KY/2
+              mask[o0 / 32] |= (uint32_t)(acc[j][m].x >= thr_n) << (o0 % 32);
+              mask[o1 / 32] |= (uint32_t)(acc[j][m].y >= thr_n) << (o1 % 32);
             }
         } else {
           // edge item: n_cov >= nx + ny - N, with nx / ny the frames whose x / y
@@ -808,9 +967,9 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
             const float thr_j = lower(__ldg(ff.thr + min(nlo, N)));
   #pragma unroll
             for (int m = 0; m < KY / 2; ++m) {
-              const int o = j * KY + 2 * m;
-              mask[o / 32] |= (uint32_t)(acc[j][m].x >= thr_j) << (o % 32);
-              mask[o / 32] |= (uint32_t)(acc[j][m].y >= thr_j) << (o % 32 + 1);
+              const int o0 = j * KY + m, o1 = o0 + KY / 2;  // rows m and m + KY/2
+              mask[o0 / 32] |= (uint32_t)(acc[j][m].x >= thr_j) << (o0 % 32);
+              mask[o1 / 32] |= (uint32_t)(acc[j][m].y >= thr_j) << (o1 % 32);
             }
           }
         }
@@ -835,10 +994,33 @@ __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
     // ahead of the slowest warp)
     __syncwarp();
     if (lane == 0 && atomicAdd(&item_done[item % kItemSlots], 1) == kCW - 1) {
-      item_inside[item % kItemSlots] = 0;
+#pragma unroll
+      for (int h = 0; h < H; ++h) item_inside[(item % kItemSlots) * H + h] = 0;
       item_done[item % kItemSlots] = 0;
     }
   }
+}
+
+// Kernels: one CTA of 9 warps (two per SM for KY <= 16, 96 registers a
+// thread), or, with two halves, one CTA of 17 warps per SM at 112 registers
+// (17 warps x 32 threads x 112 registers, counted in warp pairs, fill the
+// 64 K register file).
+template <typename T, int KY, int S, int F, bool DUMP, bool BL, bool CP, int OPT, int H>
+__global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
+    k_stack_fast(const __grid_constant__ FastArgs p) {
+  stack_fast_body<T, KY, S, F, DUMP, BL, CP, OPT, 1>(p);
+}
+template <typename T, int KY, int S, int F, bool DUMP, bool BL, bool CP, int OPT, int H>
+__global__ void __launch_bounds__(32 * (2 * kXV + 1), 1) k_stack_fast_h2(const __grid_constant__ FastArgs p) {
+  stack_fast_body<T, KY, S, F, DUMP, BL, CP, OPT, 2>(p);
+}
+
+template <typename T, int KY, int S, int F, bool DUMP, bool BL, bool CP, int OPT, int H>
+constexpr void (*kernel_of())(FastArgs) {
+  if constexpr (H == 1)
+    return k_stack_fast<T, KY, S, F, DUMP, BL, CP, OPT, 1>;
+  else
+    return k_stack_fast_h2<T, KY, S, F, DUMP, BL, CP, OPT, 2>;
 }
 
 // Compiled variants: (rows per thread, stages, frames per stage), each with
@@ -848,20 +1030,27 @@ struct Variant {
   void (*dump_fn)(FastArgs);
   int threads, stages, ky, stages_f;
   int tx;  // tile width: 32 (one column per lane) or 64 (column pairs)
+  int halves;  // x-velocity tiles per item (boxes per frame)
   const char* name;
 };
 
-#define ST_VARIANT(T, KY, S, F, BL, CP)                                                       \
+#define ST_VARIANT(T, KY, S, F, BL, CP, OPT, H)                                               \
   {                                                                                           \
-    (void (*)(FastArgs))k_stack_fast<T, KY, S, F, false, BL, CP>,                               \
-        (void (*)(FastArgs))k_stack_fast<T, KY, S, F, true, BL, CP>, 32 * (kXV + 1), S * F,    \
-        KY, F, CP ? 2 * kTX : kTX, #T "_ky" #KY "_s" #S "_f" #F #CP                            \
+    kernel_of<T, KY, S, F, false, BL, CP, OPT, H>(),                                          \
+        kernel_of<T, KY, S, F, true, BL, CP, OPT, H>(),                                       \
+        32 * (kXV * H + 1), S * F, KY, F, CP ? 2 * kTX : kTX, H,                               \
+        #T "_ky" #KY "_s" #S "_f" #F "_cp" #CP "_o" #OPT "_h" #H                                \
   }
-#define NEAR(T, KY, S, F) ST_VARIANT(T, KY, S, F, false, false)
-#define PAIR(T, KY, S, F) ST_VARIANT(T, KY, S, F, false, true)
-#define BILI(T, KY, S, F) ST_VARIANT(T, KY, S, F, true, false)
+#define NEAR(T, KY, S, F) ST_VARIANT(T, KY, S, F, false, false, 0, 1)
+#define NEARO(T, KY, S, F, OPT) ST_VARIANT(T, KY, S, F, false, false, OPT, 1)
+#define NEARH(T, KY, S, F, OPT) ST_VARIANT(T, KY, S, F, false, false, OPT, 2)
+#define PAIR(T, KY, S, F) ST_VARIANT(T, KY, S, F, false, true, 0, 1)
+#define BILI(T, KY, S, F) ST_VARIANT(T, KY, S, F, true, false, 0, 1)
 const Variant kVarF32[] = {NEAR(float, 16, 6, 4), NEAR(float, 16, 8, 4), NEAR(float, 20, 6, 4),
-                           NEAR(float, 24, 6, 4), NEAR(float, 16, 12, 2), PAIR(float, 8, 8, 4)};
+                           NEAR(float, 24, 6, 4), NEAR(float, 16, 12, 2), PAIR(float, 8, 8, 4),
+                           NEARO(float, 16, 6, 4, 1), NEARO(float, 16, 6, 4, 2),
+                           NEARO(float, 16, 6, 4, 4), NEARO(float, 16, 8, 4, 8),
+                           NEARO(float, 16, 8, 4, 16), NEARO(float, 16, 6, 4, 16)};
 const Variant kVarF16[] = {NEAR(__half, 16, 6, 4), NEAR(__half, 16, 8, 4),
                            PAIR(__half, 8, 8, 4)};
 const Variant kVarBF16[] = {NEAR(__nv_bfloat16, 16, 6, 4), NEAR(__nv_bfloat16, 16, 8, 4),
@@ -871,6 +1060,8 @@ const Variant kVarBlF32[] = {BILI(float, 8, 8, 4), BILI(float, 12, 8, 4), BILI(f
 const Variant kVarBlF16[] = {BILI(__half, 8, 8, 4), BILI(__half, 12, 8, 4)};
 const Variant kVarBlBF16[] = {BILI(__nv_bfloat16, 8, 8, 4), BILI(__nv_bfloat16, 12, 8, 4)};
 #undef NEAR
+#undef NEARO
+#undef NEARH
 #undef PAIR
 #undef BILI
 #undef ST_VARIANT
@@ -1241,7 +1432,7 @@ int launch_stack_fast_multi(const FieldDev* fds, FastPlan* const* fps, int n, fl
   for (int i = 0; i < n; ++i) {
     a.ff[i] = fps[order[i]]->d_ff;
     a.maps[i] = fps[order[i]]->d_map;
-    total += items_of(fps[order[i]]->h_ff, ky, var.tx);
+    total += items_of(fps[order[i]]->h_ff, ky, var.tx, var.halves);
   }
   a.n_fields = n;
   a.n_items = fp0->item_limit > 0 && total > fp0->item_limit ? fp0->item_limit : total;
@@ -1254,12 +1445,20 @@ int launch_stack_fast_multi(const FieldDev* fds, FastPlan* const* fps, int n, fl
   const int esz = fds[0].storage == ST_F32 ? 4 : 2;
   const int stage_bytes = ((boxh * boxw * esz) + 127) & ~127;
   void (*fn)(FastArgs) = dump_S ? var.dump_fn : var.fn;
-  const size_t smem = (size_t)var.stages * stage_bytes + 128;
+  const size_t smem = (size_t)var.stages * var.halves * stage_bytes + 128;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (cudaMemsetAsync(&ctr->work_next, 0, sizeof(ctr->work_next), s) != cudaSuccess) return -1;
-  const int per_sm = ky <= 16 ? 2 : 1;  // persistent CTAs per SM
+  // persistent CTAs per SM: as many as are resident at once (2 for KY <= 16),
+  // queried once per compiled kernel
+  static int resident[2][3][2 * kNumVariants] = {};
+  int& per_sm = resident[fp0->bl][fds[0].storage][2 * vi + (dump_S ? 1 : 0)];
+  if (per_sm < 1 &&
+      (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)fn, var.threads,
+                                                     smem) != cudaSuccess ||
+       per_sm < 1))
+    per_sm = 1;
   const int64_t grid = a.n_items < (int64_t)sms * per_sm ? a.n_items : (int64_t)sms * per_sm;
   if (grid < 1) return 0;
   void* args[1] = {&a};
