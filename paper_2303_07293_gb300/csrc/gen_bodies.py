@@ -56,7 +56,7 @@ def body(ky):
     return lines, n_acc, n_w
 
 
-def stage_loop(ky, frames, row_bytes):
+def stage_loop(ky, frames, row_bytes, stream=False):
     """The frames of one ring stage for one warp, as a PTX loop: per frame,
     the warp's word (window byte offset in the ring | pattern id << 24) is
     read from shared memory, the window's ky + 3 rows are loaded into the
@@ -80,19 +80,34 @@ def stage_loop(ky, frames, row_bytes):
          "and.b32 sa, sw, 16777215;",
          f"add.u32 sa, sa, %{lb};",
          "shr.u32 sid, sw, 24;"]
-    for r in range(ky + 3):
-        L.append(f"ld.shared.f32 sv{r}, [sa+{r * row_bytes}];")
-    for q in range(n_w):
-        L.append(f"mov.b64 sW{q}, {{sv{q}, sv{q + kh}}};")
+    if not stream:
+        for r in range(ky + 3):
+            L.append(f"ld.shared.f32 sv{r}, [sa+{r * row_bytes}];")
+        for q in range(n_w):
+            L.append(f"mov.b64 sW{q}, {{sv{q}, sv{q + kh}}};")
     L.append("BTT: .branchtargets " + ", ".join(f"BT{p}" for p in range(16)) + ";")
     L.append("brx.idx.uni sid, BTT;")
     for p in range(N_PATTERNS):
         L.append(f"BT{p}:")
-        for j in range(4):
-            c = pat_off(p, j)
-            for m in range(kh):
-                a = j * kh + m
-                L.append(f"add.rn.f32x2 %{a}, %{a}, sW{m + c};")
+        if stream:
+            loaded = set()
+            for q in range(n_w):
+                for r in (q, q + kh):
+                    if r not in loaded:
+                        L.append(f"ld.shared.f32 sv{r}, [sa+{r * row_bytes}];")
+                        loaded.add(r)
+                L.append(f"mov.b64 sW{q}, {{sv{q}, sv{q + kh}}};")
+                for j in range(4):
+                    m = q - pat_off(p, j)
+                    if 0 <= m < kh:
+                        a = j * kh + m
+                        L.append(f"add.rn.f32x2 %{a}, %{a}, sW{q};")
+        else:
+            for j in range(4):
+                c = pat_off(p, j)
+                for m in range(kh):
+                    a = j * kh + m
+                    L.append(f"add.rn.f32x2 %{a}, %{a}, sW{m + c};")
         L.append("bra.uni SNEXT;")
     L += ["BT15:", "SNEXT:", "add.u32 swp, swp, 4;", "add.u32 sfi, sfi, 1;",
           f"setp.lt.u32 sp, sfi, {frames};", "@sp bra.uni SLOOP;", "}"]
@@ -195,7 +210,7 @@ def stage_loop_regs(ky, frames, row_bytes):
     return [x for x in L if x], n_acc
 
 
-def item_loop(ky, frames, row_bytes, stages, warps, wait_ns=2000000000):
+def item_loop(ky, frames, row_bytes, stages, warps, wait_ns=2000000000, stream=True):
     """Every stage of one item for one warp, as one PTX block: per stage,
     wait on the stage's full barrier (all lanes, bounded by wait_ns of the
     global timer), run its frames (as stage_loop: the warp's word per frame,
@@ -205,7 +220,9 @@ def item_loop(ky, frames, row_bytes, stages, warps, wait_ns=2000000000):
     out); then the number of stages, whether the first stage's wait is
     already done, the address of this warp's words in slot 0, the lane's
     base address in the ring, and the addresses of full and empty barrier 0.
-    Slot s's words are at words0 + s*warps*frames*4; barriers 8 bytes apart."""
+    Slot s's words are at words0 + s*warps*frames*4; barriers 8 bytes apart.
+    With stream, each pattern body loads the window rows as it adds them
+    (see stage_loop_stream), which keeps few window registers live."""
     kh = ky // 2
     n_acc = 4 * kh
     n_w = kh + 3
@@ -213,14 +230,13 @@ def item_loop(ky, frames, row_bytes, stages, warps, wait_ns=2000000000):
     nst, skip, wb0, lb, fb0, eb0 = (n_acc + 3 + i for i in range(6))
     wstride = warps * frames * 4
     L = ["{",
-         ".reg .u32 sfi, sw, sa, sid, swp, sst, sbar, sln;",
-         ".reg .u64 st0, st1;",
+         ".reg .u32 sfi, sw, sa, sid, swp, sst, sbar, st0, st1;",
          f".reg .f32 sv<{ky + 3}>;",
          f".reg .b64 sW<{n_w}>;",
          ".reg .pred sp, swt, sall, slane, sany;",
+         f"mov.u32 %{err}, %laneid;",
+         f"setp.eq.u32 slane, %{err}, 0;",
          f"mov.u32 %{err}, 0;",
-         "mov.u32 sln, %laneid;",
-         "setp.eq.u32 slane, sln, 0;",
          "mov.u32 sst, 0;",
          f"setp.ge.u32 sp, sst, %{nst};",
          "@sp bra.uni IEND;",
@@ -233,14 +249,14 @@ def item_loop(ky, frames, row_bytes, stages, warps, wait_ns=2000000000):
          f"mbarrier.try_wait.parity.shared::cta.b64 swt, [sbar], %{ph};",
          "vote.sync.all.pred sall, swt, 0xffffffff;",
          "@sall bra.uni IRUN;",
-         "mov.u64 st0, %globaltimer;",
+         "mov.u32 st0, %globaltimer_lo;",
          "IWAIT:",
          f"mbarrier.try_wait.parity.shared::cta.b64 swt, [sbar], %{ph};",
          "vote.sync.all.pred sall, swt, 0xffffffff;",
          "@sall bra.uni IRUN;",
-         "mov.u64 st1, %globaltimer;",
-         "sub.u64 st1, st1, st0;",
-         f"setp.gt.u64 sp, st1, {wait_ns};",
+         "mov.u32 st1, %globaltimer_lo;",
+         "sub.u32 st1, st1, st0;",  # modulo 2^32 ns: exact below 4.29 s
+         f"setp.gt.u32 sp, st1, {wait_ns};",
          "vote.sync.any.pred sany, sp, 0xffffffff;",
          "@!sany bra.uni IWAIT;",
          f"mov.u32 %{err}, 1;",
@@ -253,19 +269,34 @@ def item_loop(ky, frames, row_bytes, stages, warps, wait_ns=2000000000):
          "and.b32 sa, sw, 16777215;",
          f"add.u32 sa, sa, %{lb};",
          "shr.u32 sid, sw, 24;"]
-    for r in range(ky + 3):
-        L.append(f"ld.shared.f32 sv{r}, [sa+{r * row_bytes}];")
-    for q in range(n_w):
-        L.append(f"mov.b64 sW{q}, {{sv{q}, sv{q + kh}}};")
+    if not stream:
+        for r in range(ky + 3):
+            L.append(f"ld.shared.f32 sv{r}, [sa+{r * row_bytes}];")
+        for q in range(n_w):
+            L.append(f"mov.b64 sW{q}, {{sv{q}, sv{q + kh}}};")
     L.append("BTT: .branchtargets " + ", ".join(f"BT{p}" for p in range(16)) + ";")
     L.append("brx.idx.uni sid, BTT;")
     for p in range(N_PATTERNS):
         L.append(f"BT{p}:")
-        for j in range(4):
-            c = pat_off(p, j)
-            for m in range(kh):
-                a = j * kh + m
-                L.append(f"add.rn.f32x2 %{a}, %{a}, sW{m + c};")
+        if stream:
+            loaded = set()
+            for q in range(n_w):
+                for r in (q, q + kh):
+                    if r not in loaded:
+                        L.append(f"ld.shared.f32 sv{r}, [sa+{r * row_bytes}];")
+                        loaded.add(r)
+                L.append(f"mov.b64 sW{q}, {{sv{q}, sv{q + kh}}};")
+                for j in range(4):
+                    m = q - pat_off(p, j)
+                    if 0 <= m < kh:
+                        a = j * kh + m
+                        L.append(f"add.rn.f32x2 %{a}, %{a}, sW{q};")
+        else:
+            for j in range(4):
+                c = pat_off(p, j)
+                for m in range(kh):
+                    a = j * kh + m
+                    L.append(f"add.rn.f32x2 %{a}, %{a}, sW{m + c};")
         L.append("bra.uni SNEXT;")
     L += ["BT15:", "SNEXT:", "add.u32 swp, swp, 4;", "add.u32 sfi, sfi, 1;",
           f"setp.lt.u32 sp, sfi, {frames};", "@sp bra.uni SLOOP;",
@@ -285,6 +316,8 @@ def item_loop(ky, frames, row_bytes, stages, warps, wait_ns=2000000000):
 
 
 ITEMS = ((16, 4, 160, 8, 8), (16, 4, 160, 6, 8))  # (KY, F, row bytes, S, consumer warps)
+# window-first bodies (all rows loaded before the indexed branch) for comparison
+ITEMS_WINDOW = ((16, 4, 160, 8, 8),)
 
 
 def render():
@@ -332,6 +365,12 @@ def render():
     for ky, frames, row_bytes, stages, warps in ITEMS:
         lines, n_acc = item_loop(ky, frames, row_bytes, stages, warps)
         out.append(f"#define ST_ITEM_KY{ky}_F{frames}_R{row_bytes}_S{stages}_W{warps} \\")
+        for ln in lines:
+            out.append(f'  "{ln}\\n\\t" \\')
+        out.append("")
+    for ky, frames, row_bytes, stages, warps in ITEMS_WINDOW:
+        lines, n_acc = item_loop(ky, frames, row_bytes, stages, warps, stream=False)
+        out.append(f"#define ST_ITEMW_KY{ky}_F{frames}_R{row_bytes}_S{stages}_W{warps} \\")
         for ln in lines:
             out.append(f'  "{ln}\\n\\t" \\')
         out.append("")

@@ -619,10 +619,10 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
       if (lane == 0) atomicOr(&p.ctr->error, ERR_TIMEOUT);  // leave (warp-uniform)
       break;
     }
-    const Item it = item_info[item % kItemSlots];
+    Item it = item_info[item % kItemSlots];
     if (it.f < 0) break;  // end of the work
-    const FastField& ff = *p.ff[it.f];
-    const int N = ff.N;
+    const FastField* ffp = p.ff[it.f];
+    int N = ffp->N;
     const int spi = (N + F - 1) / F;
     float2 acc[kMB][kAccN];
 #pragma unroll
@@ -641,11 +641,15 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
       static_assert(KY == 16 && F == 4 && kCW == 8 && sizeof(T) == 4 && (S == 8 || S == 6),
                     "the item loop is generated for FP32, KY = 16, F = 4, 8 warps, S = 6 or 8");
       uint32_t slot = (uint32_t)c_slot, ph = c_ph, err = 0;
+      __syncwarp();  // the item description is read before the block
       const uint32_t wb0 = smem_u32(&slot_word[warp * F]);
       const uint32_t lb = smem_u32(smem) + lane * (uint32_t)sizeof(T);
       const uint32_t fb0 = smem_u32(&full_bar[0]), eb0 = smem_u32(&empty_bar[0]);
       const uint32_t nst = (uint32_t)spi, skip = 1u;
-      if constexpr (S == 8)
+      if constexpr (S == 8 && (OPT & 32) != 0)
+        asm volatile(ST_ITEMW_KY16_F4_R160_S8_W8
+                     ST_ITEM_OPERANDS_KY16(acc64, slot, ph, err, nst, skip, wb0, lb, fb0, eb0));
+      else if constexpr (S == 8)
         asm volatile(ST_ITEM_KY16_F4_R160_S8_W8
                      ST_ITEM_OPERANDS_KY16(acc64, slot, ph, err, nst, skip, wb0, lb, fb0, eb0));
       else
@@ -657,7 +661,13 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
         if (lane == 0) atomicOr(&p.ctr->error, ERR_TIMEOUT);
         ok = false;
       }
+      // read the item again (still in its slot: the producer is fewer than
+      // kItemSlots items ahead), so nothing of it stays live across the block
+      it = item_info[item % kItemSlots];
+      ffp = p.ff[it.f];
+      N = ffp->N;
     }
+    const FastField& ff = *ffp;
     for (int st = 0; st < (kItemPtx ? 0 : spi); ++st) {
       if (st > 0 && !__all_sync(0xffffffffu, mbar_wait(&full_bar[c_slot], c_ph, kWaitNs))) {
         if (lane == 0) atomicOr(&p.ctr->error, ERR_TIMEOUT);
@@ -1044,13 +1054,13 @@ struct Variant {
 #define NEAR(T, KY, S, F) ST_VARIANT(T, KY, S, F, false, false, 0, 1)
 #define NEARO(T, KY, S, F, OPT) ST_VARIANT(T, KY, S, F, false, false, OPT, 1)
 #define NEARH(T, KY, S, F, OPT) ST_VARIANT(T, KY, S, F, false, false, OPT, 2)
+// the whole item's stages in one PTX block, pattern bodies that load the
+// window rows as they add them (FP32, KY = 16, F = 4)
+#define ITEM(T, KY, S, F) ST_VARIANT(T, KY, S, F, false, false, 16, 1)
 #define PAIR(T, KY, S, F) ST_VARIANT(T, KY, S, F, false, true, 0, 1)
 #define BILI(T, KY, S, F) ST_VARIANT(T, KY, S, F, true, false, 0, 1)
-const Variant kVarF32[] = {NEAR(float, 16, 6, 4), NEAR(float, 16, 8, 4), NEAR(float, 20, 6, 4),
-                           NEAR(float, 24, 6, 4), NEAR(float, 16, 12, 2), PAIR(float, 8, 8, 4),
-                           NEARO(float, 16, 6, 4, 1), NEARO(float, 16, 6, 4, 2),
-                           NEARO(float, 16, 6, 4, 4), NEARO(float, 16, 8, 4, 8),
-                           NEARO(float, 16, 8, 4, 16), NEARO(float, 16, 6, 4, 16)};
+const Variant kVarF32[] = {ITEM(float, 16, 8, 4), ITEM(float, 16, 6, 4), NEAR(float, 16, 8, 4),
+                           NEAR(float, 24, 6, 4), PAIR(float, 8, 8, 4)};
 const Variant kVarF16[] = {NEAR(__half, 16, 6, 4), NEAR(__half, 16, 8, 4),
                            PAIR(__half, 8, 8, 4)};
 const Variant kVarBF16[] = {NEAR(__nv_bfloat16, 16, 6, 4), NEAR(__nv_bfloat16, 16, 8, 4),
@@ -1062,6 +1072,7 @@ const Variant kVarBlBF16[] = {BILI(__nv_bfloat16, 8, 8, 4), BILI(__nv_bfloat16, 
 #undef NEAR
 #undef NEARO
 #undef NEARH
+#undef ITEM
 #undef PAIR
 #undef BILI
 #undef ST_VARIANT

@@ -43,7 +43,7 @@ def test_patterns_are_the_15_monotone_staircases():
 
 def test_item_loop_bodies_add_window_pair_m_plus_c():
     g = _gen()
-    lines, n_acc = g.item_loop(16, 4, 160, 8, 8)
+    lines, n_acc = g.item_loop(16, 4, 160, 8, 8, stream=False)
     text = "\n".join(lines)
     kh = 8
     for p in range(15):
