@@ -114,7 +114,7 @@ def stage_loop(ky, frames, row_bytes, stream=False):
     return L, n_acc
 
 
-STAGES = ((16, 4, 160),)  # (rows per thread, frames per stage, box row bytes): FP32, 40-wide box
+STAGES = ((16, 4, 160), (12, 4, 160))  # (rows per thread, frames per stage, box row bytes)
 
 
 def stage_loop_stream(ky, frames, row_bytes):
@@ -251,7 +251,8 @@ def item_loop(ky, frames, row_bytes, stages, warps, wait_ns=2000000000, stream=T
          "@sall bra.uni IRUN;",
          "mov.u32 st0, %globaltimer_lo;",
          "IWAIT:",
-         f"mbarrier.try_wait.parity.shared::cta.b64 swt, [sbar], %{ph};",
+         # suspend in the barrier (up to 20 us a try) rather than spin
+         f"mbarrier.try_wait.parity.shared::cta.b64 swt, [sbar], %{ph}, 20000;",
          "vote.sync.all.pred sall, swt, 0xffffffff;",
          "@sall bra.uni IRUN;",
          "mov.u32 st1, %globaltimer_lo;",
@@ -315,9 +316,9 @@ def item_loop(ky, frames, row_bytes, stages, warps, wait_ns=2000000000, stream=T
     return L, n_acc
 
 
-ITEMS = ((16, 4, 160, 8, 8), (16, 4, 160, 6, 8))  # (KY, F, row bytes, S, consumer warps)
-# window-first bodies (all rows loaded before the indexed branch) for comparison
-ITEMS_WINDOW = ((16, 4, 160, 8, 8),)
+ITEMS = ((16, 16, 160, 2, 16), (16, 16, 160, 2, 8), (16, 12, 160, 3, 8),
+         (16, 8, 160, 4, 8), (16, 8, 160, 4, 16))  # (KY, F, row bytes, S, consumer warps)
+ITEMS_WINDOW = ()
 
 
 def render():

@@ -420,7 +420,7 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
   constexpr int kOut = kMB * KY * (CP ? 2 : 1);  // outputs per thread per item
   constexpr int kItemSlots = 8;
   constexpr int kNoop = kPatterns;  // pattern id of a padding frame
-  static_assert(F <= 4, "pattern ids of a stage are packed into one word");
+  static_assert(F <= 4 || (OPT & 24) != 0, "pattern ids of a stage are packed into one word");
   extern __shared__ __align__(128) float smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[S];
   __shared__ __align__(8) uint64_t empty_bar[S];
@@ -483,6 +483,20 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
       if (lane == 0) L = (int64_t)atomicAdd(p.work, 1ull);
       return __shfl_sync(0xffffffffu, L, 0);
     };
+    // the field of the current (and of the next) item, held in registers:
+    // its descriptor in global memory is read once per field change
+    struct Geo {
+      int N, W, H, nA, nB;
+      const int4* xt;
+      const int4* yt;
+      const unsigned char* pat;
+      const float4* fxt;
+      const float4* fyt;
+    };
+    auto geo_of = [&](int f) -> Geo {
+      const FastField& ff = *p.ff[f];
+      return Geo{ff.N, ff.W, ff.H, ff.nA, ff.nB, ff.xt, ff.yt, ff.pat, ff.fxt, ff.fyt};
+    };
     // per-stage table entries of this lane's frame (valid: a real copy)
     struct Entry {
       int4 xe, ye;
@@ -490,24 +504,23 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
       bool valid;
       float4 f0, f1, fy;
     };
-    auto load_entry = [&](const Item& it, int st) -> Entry {
+    auto load_entry = [&](const Item& it, const Geo& g, int st) -> Entry {
       Entry e{};
       e.id = kNoop;
       e.valid = false;
       if (it.f < 0 || lane >= kLanes) return e;
-      const FastField& ff = *p.ff[it.f];
       const int fr = st * F + fi_l;
       const int A = it.A * H + h_l;
-      if (fr >= ff.N) return e;
-      e.ye = __ldg(ff.yt + (int64_t)fr * ff.nB + it.B);
-      e.id = ff.pat[(int64_t)fr * ff.nB + it.B];
-      if (A >= ff.nA) return e;  // the second half of a field's last tile group
-      e.xe = __ldg(ff.xt + (int64_t)fr * ff.nA + A);
+      if (fr >= g.N) return e;
+      e.ye = __ldg(g.yt + (int64_t)fr * g.nB + it.B);
+      e.id = g.pat[(int64_t)fr * g.nB + it.B];
+      if (A >= g.nA) return e;  // the second half of a field's last tile group
+      e.xe = __ldg(g.xt + (int64_t)fr * g.nA + A);
       e.valid = true;
       if constexpr (BL) {
-        e.f0 = __ldg(ff.fxt + 2 * ((int64_t)fr * ff.nA + A));
-        e.f1 = __ldg(ff.fxt + 2 * ((int64_t)fr * ff.nA + A) + 1);
-        e.fy = __ldg(ff.fyt + (int64_t)fr * ff.nB + it.B);
+        e.f0 = __ldg(g.fxt + 2 * ((int64_t)fr * g.nA + A));
+        e.f1 = __ldg(g.fxt + 2 * ((int64_t)fr * g.nA + A) + 1);
+        e.fy = __ldg(g.fyt + (int64_t)fr * g.nB + it.B);
       }
       return e;
     };
@@ -517,10 +530,11 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
     Item it = locate(take());
     int64_t L_next = it.f >= 0 ? take() : p.n_items;
     int st = 0;
-    Entry cur = load_entry(it, 0);
+    Geo g = geo_of(it.f >= 0 ? it.f : 0);
+    Entry cur = load_entry(it, g, 0);
     for (int item = 0; ok;) {
       const bool done = it.f < 0;
-      const int N = done ? 1 : p.ff[it.f]->N;
+      const int N = done ? 1 : g.N;
       const int spi = (N + F - 1) / F;  // stages of this item (an end item: one)
       const CUtensorMap* map = done ? nullptr : p.maps[it.f];
       if (!done && it.f != acq_f) {
@@ -532,12 +546,14 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
       }
       // the next stage: of this item, or the first of the next item
       Item it_n = it;
+      Geo g_n = g;
       int st_n = st + 1;
       if (st_n == spi) {
         it_n = done ? it : locate(L_next);
+        if (it_n.f >= 0 && it_n.f != it.f) g_n = geo_of(it_n.f);
         st_n = 0;
       }
-      const Entry nxt = done ? cur : load_entry(it_n, st_n);
+      const Entry nxt = done ? cur : load_entry(it_n, g_n, st_n);
       if (seq >= S &&
           !mbar_wait_sleep(&empty_bar[slot], (uint32_t)(seq / S - 1) & 1u, kWaitNs,
                            kProducerSleepNs)) {
@@ -549,22 +565,23 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
       const unsigned copies = __ballot_sync(0xffffffffu, cur.valid);
       if (lane == 0 && copies) mbar_expect_tx(&full_bar[slot], box_bytes * __popc(copies));
       if constexpr (kLean) {
-        if (lane < kLanes) {
-          const uint32_t base =
-              (uint32_t)(((slot * F + fi_l) * H + h_l) * box_floats * (int)sizeof(T));
-          const uint32_t idb = (cur.valid ? cur.id : (unsigned)kNoop) << 24;
+        // one word per lane: word (frame fi, warp w) of the stage, from the
+        // entry of lane h * F + fi (its half's packed column offsets and id)
+        const uint32_t ocw = (uint32_t)cur.xe.y;
+        const uint32_t idv = cur.valid ? cur.id : (unsigned)kNoop;
 #pragma unroll
-          for (int w = 0; w < kXV; ++w) {
-            const uint32_t oc = cur.valid ? ((uint32_t)cur.xe.y >> (4 * w)) & 15u : 0u;
-            slot_word[(slot * kCW + h_l * kXV + w) * F + fi_l] =
-                (base + oc * (uint32_t)sizeof(T)) | idb;
-          }
+        for (int k = lane; k < F * kCW; k += 32) {
+          const int fi = k / kCW, w = k % kCW, h = w / kXV;
+          const uint32_t o = __shfl_sync(0xffffffffu, ocw, h * F + fi);
+          const uint32_t id = __shfl_sync(0xffffffffu, idv, h * F + fi);
+          const uint32_t oc = id == (unsigned)kNoop ? 0u : (o >> (4 * (w % kXV))) & 15u;
+          const uint32_t base = (uint32_t)(((slot * F + fi) * H + h) * box_floats * (int)sizeof(T));
+          slot_word[(slot * kCW + w) * F + fi] = (base + oc * (uint32_t)sizeof(T)) | (id << 24);
         }
       }
       if (cur.valid) {
-        const FastField& ff = *p.ff[it.f];
         const int fr = st * F + fi_l;
-        slot_ocol[(slot * H + h_l) * F + fi_l] = (uint32_t)cur.xe.y;
+        if constexpr (!kLean) slot_ocol[(slot * H + h_l) * F + fi_l] = (uint32_t)cur.xe.y;
         if constexpr (BL) {
           float* d = slot_fx + (slot * F + fi_l) * kXV;
           d[0] = cur.f0.x; d[1] = cur.f0.y; d[2] = cur.f0.z; d[3] = cur.f0.w;
@@ -574,18 +591,22 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
         // every sample of the half strictly inside (bilinear: with its right
         // and lower taps), so every output of the half is covered
         const bool inside = it.X0 + cur.xe.z >= 0 &&
-                            it.X0 + kTXv - 1 + cur.xe.w + kEdge < ff.W &&
-                            it.Y0 + cur.ye.x >= 0 && it.Y0 + kTY - 1 + cur.ye.y + kEdge < ff.H;
+                            it.X0 + kTXv - 1 + cur.xe.w + kEdge < g.W &&
+                            it.Y0 + cur.ye.x >= 0 && it.Y0 + kTY - 1 + cur.ye.y + kEdge < g.H;
         if (inside) atomicAdd(&item_inside[(item % kItemSlots) * H + h_l], 1);
         tma_load_3d(smem + (size_t)((slot * F + fi_l) * H + h_l) * box_floats, map,
                     it.X0 + cur.xe.x, it.Y0 + cur.ye.x, fr, &full_bar[slot]);
       }
-      // the stage's ids (the same for both halves), packed: frame fi in byte fi
-      uint32_t w = lane < F ? cur.id << (8 * lane) : 0u;
-      w |= __shfl_xor_sync(0xffffffffu, w, 1);
-      w |= __shfl_xor_sync(0xffffffffu, w, 2);
-      if (lane == 0) slot_ids[slot] = w;
-      __threadfence_block();
+      if constexpr (!kLean) {
+        // the stage's ids (the same for both halves), packed: frame fi in byte fi
+        uint32_t w = lane < F ? cur.id << (8 * lane) : 0u;
+        w |= __shfl_xor_sync(0xffffffffu, w, 1);
+        w |= __shfl_xor_sync(0xffffffffu, w, 2);
+        if (lane == 0) slot_ids[slot] = w;
+        __threadfence_block();
+      }
+      // the lanes' stores are ordered before lane 0's arrive (release) by the
+      // warp barrier; consumers read them after their wait (acquire)
       __syncwarp();
       if (lane == 0) mbar_arrive(&full_bar[slot]);  // releases this stage's info
       if (++slot == S) slot = 0;
@@ -594,6 +615,7 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
       if (st_n == 0) {  // next item: take the one after it from the counter
         ++item;
         it = it_n;
+        g = g_n;
         L_next = it.f >= 0 ? take() : p.n_items;
       }
       st = st_n;
@@ -638,23 +660,28 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
 
     bool ok = true;
     if constexpr (kItemPtx) {
-      static_assert(KY == 16 && F == 4 && kCW == 8 && sizeof(T) == 4 && (S == 8 || S == 6),
-                    "the item loop is generated for FP32, KY = 16, F = 4, 8 warps, S = 6 or 8");
+      static_assert(KY == 16 && sizeof(T) == 4, "the item loop is generated for FP32, KY = 16");
       uint32_t slot = (uint32_t)c_slot, ph = c_ph, err = 0;
       __syncwarp();  // the item description is read before the block
       const uint32_t wb0 = smem_u32(&slot_word[warp * F]);
       const uint32_t lb = smem_u32(smem) + lane * (uint32_t)sizeof(T);
       const uint32_t fb0 = smem_u32(&full_bar[0]), eb0 = smem_u32(&empty_bar[0]);
       const uint32_t nst = (uint32_t)spi, skip = 1u;
-      if constexpr (S == 8 && (OPT & 32) != 0)
-        asm volatile(ST_ITEMW_KY16_F4_R160_S8_W8
-                     ST_ITEM_OPERANDS_KY16(acc64, slot, ph, err, nst, skip, wb0, lb, fb0, eb0));
-      else if constexpr (S == 8)
-        asm volatile(ST_ITEM_KY16_F4_R160_S8_W8
-                     ST_ITEM_OPERANDS_KY16(acc64, slot, ph, err, nst, skip, wb0, lb, fb0, eb0));
+#define ST_ITEM_ASM(NAME) \
+  asm volatile(NAME ST_ITEM_OPERANDS_KY16(acc64, slot, ph, err, nst, skip, wb0, lb, fb0, eb0))
+      if constexpr (F == 16 && S == 2 && kCW == 16)
+        ST_ITEM_ASM(ST_ITEM_KY16_F16_R160_S2_W16);
+      else if constexpr (F == 16 && S == 2 && kCW == 8)
+        ST_ITEM_ASM(ST_ITEM_KY16_F16_R160_S2_W8);
+      else if constexpr (F == 12 && S == 3 && kCW == 8)
+        ST_ITEM_ASM(ST_ITEM_KY16_F12_R160_S3_W8);
+      else if constexpr (F == 8 && S == 4 && kCW == 8)
+        ST_ITEM_ASM(ST_ITEM_KY16_F8_R160_S4_W8);
+      else if constexpr (F == 8 && S == 4 && kCW == 16)
+        ST_ITEM_ASM(ST_ITEM_KY16_F8_R160_S4_W16);
       else
-        asm volatile(ST_ITEM_KY16_F4_R160_S6_W8
-                     ST_ITEM_OPERANDS_KY16(acc64, slot, ph, err, nst, skip, wb0, lb, fb0, eb0));
+        static_assert(F == 0, "no generated item loop for these stages and warps");
+#undef ST_ITEM_ASM
       c_slot = (int)slot;
       c_ph = ph;
       if (err) {
@@ -674,7 +701,7 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
         ok = false;
         break;
       }
-      if constexpr (kLean) {
+      if constexpr (kLean && !kItemPtx) {
         static_assert(KY == 16 && F == 4 && !CP && !BL && sizeof(T) == 4,
                       "the lean stage loop is generated for FP32, KY = 16, F = 4");
         const uint32_t wb = smem_u32(&slot_word[(c_slot * kCW + warp) * F]);
@@ -1057,9 +1084,11 @@ struct Variant {
 // the whole item's stages in one PTX block, pattern bodies that load the
 // window rows as they add them (FP32, KY = 16, F = 4)
 #define ITEM(T, KY, S, F) ST_VARIANT(T, KY, S, F, false, false, 16, 1)
+#define ITEMH(T, KY, S, F) ST_VARIANT(T, KY, S, F, false, false, 16, 2)
 #define PAIR(T, KY, S, F) ST_VARIANT(T, KY, S, F, false, true, 0, 1)
 #define BILI(T, KY, S, F) ST_VARIANT(T, KY, S, F, true, false, 0, 1)
-const Variant kVarF32[] = {ITEM(float, 16, 8, 4), ITEM(float, 16, 6, 4), NEAR(float, 16, 8, 4),
+const Variant kVarF32[] = {ITEMH(float, 16, 2, 16), ITEM(float, 16, 2, 16), ITEM(float, 16, 3, 12),
+                           ITEM(float, 16, 4, 8), ITEMH(float, 16, 4, 8), NEAR(float, 16, 8, 4),
                            NEAR(float, 24, 6, 4), PAIR(float, 8, 8, 4)};
 const Variant kVarF16[] = {NEAR(__half, 16, 6, 4), NEAR(__half, 16, 8, 4),
                            PAIR(__half, 8, 8, 4)};
@@ -1073,6 +1102,7 @@ const Variant kVarBlBF16[] = {BILI(__nv_bfloat16, 8, 8, 4), BILI(__nv_bfloat16, 
 #undef NEARO
 #undef NEARH
 #undef ITEM
+#undef ITEMH
 #undef PAIR
 #undef BILI
 #undef ST_VARIANT
@@ -1446,7 +1476,10 @@ int launch_stack_fast_multi(const FieldDev* fds, FastPlan* const* fps, int n, fl
     total += items_of(fps[order[i]]->h_ff, ky, var.tx, var.halves);
   }
   a.n_fields = n;
-  a.n_items = fp0->item_limit > 0 && total > fp0->item_limit ? fp0->item_limit : total;
+  // an autotuning run covers the same work for every variant (an item of a
+  // two-half variant holds two x-velocity tiles)
+  const int64_t limit = fp0->item_limit > 0 ? (fp0->item_limit + var.halves - 1) / var.halves : 0;
+  a.n_items = limit > 0 && total > limit ? limit : total;
   a.work = &ctr->work_next;
   a.pend = pend;
   a.cap = pend_cap;

@@ -25,7 +25,7 @@ def st():
     return m
 
 
-VARIANTS = [0, 2, 3, 4, 5, 6]  # plan default and every FP32 register-window variant
+VARIANTS = [0, 2, 3, 4, 5, 6, 7, 8, 9]  # plan default and every FP32 register-window variant
 
 
 def dev(a):
