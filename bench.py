@@ -45,24 +45,27 @@ METRIC = "G pixel*frame*velocity adds/s (2048x2048x256, 801x801 grid)"
 
 # DRAM bytes (read + write) of one stack-kernel launch, from one ncu capture
 # of `--metrics dram__bytes_read.sum,dram__bytes_write.sum` (profiles/
-# stack_speculoos_2048x256_traffic.md), with the SHA-1 prefix of the code of
-# k_stack_fast.cu it was taken on (comments and blank lines removed, so only
-# a change of the code itself retires the figure): reported only while the
-# code is that one.
+# stack_speculoos_2048x256_traffic.md), keyed by workload, storage, sampling
+# and the kernel variant that ran, with the SHA-1 prefix of the kernel's code
+# it was taken on (k_stack_fast.cu and its generated PTX bodies, comments and
+# blank lines removed, so only a change of the code itself retires the
+# figure): reported only while the code is that one.
 STACK_TRAFFIC = {
-    ("speculoos", "f32", "nearest"): (54.27e9 + 371.06e6, "4489341ce839"),
+    ("speculoos", "f32", "nearest", "float_ky16_s2_f16_cp0_o16_h2"):
+        (44.928032e9 + 355.626752e6, "08324d5c0a0a"),
 }
 
 
 def stack_source_sha():
     import hashlib
-    path = os.path.join(ROOT, "paper_2303_07293_gb300", "csrc", "k_stack_fast.cu")
     code = []
-    with open(path) as fh:
-        for line in fh:
-            line = line.split("//", 1)[0].strip()
-            if line:
-                code.append(line)
+    for name in ("k_stack_fast.cu", "st_bodies.inc"):
+        path = os.path.join(ROOT, "paper_2303_07293_gb300", "csrc", name)
+        with open(path) as fh:
+            for line in fh:
+                line = line.split("//", 1)[0].strip()
+                if line:
+                    code.append(line)
     return hashlib.sha1("\n".join(code).encode()).hexdigest()[:12]
 
 
@@ -736,13 +739,16 @@ def main():
     max_mhz = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
     peak_t = sms * 128 * max_mhz * 1e6 / 1e12  # FP32 adds (or FMAs) per second, T
     stack_avg_ms = stack_ms / max(stack_launch, 1)
-    tr = STACK_TRAFFIC.get((args.workload, args.storage, args.mode))
+    variant = plan.stack_variant_name(0)
+    config["stack_variant"] = variant
+    tr = STACK_TRAFFIC.get((args.workload, args.storage, args.mode, variant))
     traffic = tr[0] if tr and tr[1] == stack_source_sha() and stack_launch == args.steps \
-        else None
+        and (args.width, args.frames, args.nv) == (None, None, None) else None
     if traffic is not None:
         traffic_note = "DRAM bytes of one launch from the stored ncu capture of this code"
     elif tr is None:
-        traffic_note = "null: no ncu DRAM capture stored for this workload"
+        traffic_note = (f"null: no ncu DRAM capture stored for this workload and variant "
+                        f"({variant})")
     elif tr[1] != stack_source_sha():
         traffic_note = (f"null: the stored capture ({tr[0] / 1e9:.2f} GB per launch) was taken "
                         f"on k_stack_fast.cu code {tr[1]}, the kernel is now "

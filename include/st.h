@@ -290,6 +290,13 @@ st_status st_last_stack_kernel_time(const st_plan_t* plan, double* ms, int64_t* 
  * 1 = register-window kernel, 0 = direct-gather kernel, -1 = no search yet. */
 int32_t st_last_stack_variant(const st_plan_t* plan, int32_t field);
 
+/* Name of the stack kernel field f used in the last search on this plan:
+ * "direct-gather", the register-window variant's name (storage type, rows
+ * per thread, ring stages, frames per stage, column pairs, code options,
+ * x-velocity tiles per block), or "?" before any search.  The string is
+ * static (owned by the library). */
+const char* st_stack_variant_name(const st_plan_t* plan, int32_t field);
+
 /* 1 if the device part of the last search (normalisation, stack, local
  * maxima) ran as a CUDA graph (use_graph: captured on the first search with
  * given frame pointers and timestamps, replayed while they stay the same),

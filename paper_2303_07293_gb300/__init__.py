@@ -82,6 +82,8 @@ def lib():
         L.st_last_stack_kernel_time.argtypes = [P, P, P]
         L.st_last_stack_variant.argtypes = [P, C.c_int32]
         L.st_last_stack_variant.restype = C.c_int32
+        L.st_stack_variant_name.argtypes = [P, C.c_int32]
+        L.st_stack_variant_name.restype = C.c_char_p
         L.st_last_graph_replayed.argtypes = [P]
         L.st_last_graph_replayed.restype = C.c_int32
         L.st_probe_add_rate.argtypes = [C.c_int32, C.c_int32, P, P]
@@ -287,6 +289,10 @@ class Plan:
         _check(lib().st_refine_eval(self._h, _ptr(theta), _ptr(centre), _ptr(field), n, fwhm,
                                     _ptr(J), _ptr(snr), _ptr(g) if grad else None))
         return J, snr, g
+
+    def stack_variant_name(self, field=0):
+        """Name of the stack kernel variant field `field` used in the last search."""
+        return lib().st_stack_variant_name(self._h, field).decode()
 
     def last_stack_variant(self, field=0):
         """1 if field used the register-window kernel in the last search, 0 if

@@ -89,7 +89,20 @@ def stage_loop(ky, frames, row_bytes, stream=False):
     L.append("brx.idx.uni sid, BTT;")
     for p in range(N_PATTERNS):
         L.append(f"BT{p}:")
-        if stream:
+        if stream and single_use:
+            used = {q for q in range(n_w) for j in range(4) if 0 <= q - pat_off(p, j) < kh}
+            for q in range(n_w):
+                if q not in used:
+                    continue
+                L.append(f"ld.shared.f32 sl{q}, [sa+{q * row_bytes}];")
+                L.append(f"ld.shared.f32 sh{q}, [sa+{(q + kh) * row_bytes}];")
+                L.append(f"mov.b64 sW{q}, {{sl{q}, sh{q}}};")
+                for j in range(4):
+                    m = q - pat_off(p, j)
+                    if 0 <= m < kh:
+                        a = j * kh + m
+                        L.append(f"add.rn.f32x2 %{a}, %{a}, sW{q};")
+        elif stream:
             loaded = set()
             for q in range(n_w):
                 for r in (q, q + kh):
@@ -210,7 +223,8 @@ def stage_loop_regs(ky, frames, row_bytes):
     return [x for x in L if x], n_acc
 
 
-def item_loop(ky, frames, row_bytes, stages, warps, wait_ns=2000000000, stream=True):
+def item_loop(ky, frames, row_bytes, stages, warps, wait_ns=2000000000, stream=True,
+              single_use=False):
     """Every stage of one item for one warp, as one PTX block: per stage,
     wait on the stage's full barrier (all lanes, bounded by wait_ns of the
     global timer), run its frames (as stage_loop: the warp's word per frame,
@@ -222,7 +236,10 @@ def item_loop(ky, frames, row_bytes, stages, warps, wait_ns=2000000000, stream=T
     base address in the ring, and the addresses of full and empty barrier 0.
     Slot s's words are at words0 + s*warps*frames*4; barriers 8 bytes apart.
     With stream, each pattern body loads the window rows as it adds them
-    (see stage_loop_stream), which keeps few window registers live."""
+    (see stage_loop_stream), which keeps few window registers live; with
+    single_use, a row that sits in two pairs (rows ky/2 .. ky/2 + 2) is
+    loaded once for each, so every loaded register is one half of one pair
+    and no register copies are needed to form the pairs."""
     kh = ky // 2
     n_acc = 4 * kh
     n_w = kh + 3
@@ -231,8 +248,10 @@ def item_loop(ky, frames, row_bytes, stages, warps, wait_ns=2000000000, stream=T
     wstride = warps * frames * 4
     L = ["{",
          ".reg .u32 sfi, sw, sa, sid, swp, sst, sbar, st0, st1;",
-         f".reg .f32 sv<{ky + 3}>;",
-         f".reg .b64 sW<{n_w}>;",
+         f".reg .f32 sv<{ky + 3}>;"]
+    if single_use:
+        L.append(f".reg .f32 sl<{n_w}>, sh<{n_w}>;")
+    L += [f".reg .b64 sW<{n_w}>;",
          ".reg .pred sp, swt, sall, slane, sany;",
          f"mov.u32 %{err}, %laneid;",
          f"setp.eq.u32 slane, %{err}, 0;",
@@ -279,7 +298,20 @@ def item_loop(ky, frames, row_bytes, stages, warps, wait_ns=2000000000, stream=T
     L.append("brx.idx.uni sid, BTT;")
     for p in range(N_PATTERNS):
         L.append(f"BT{p}:")
-        if stream:
+        if stream and single_use:
+            used = {q for q in range(n_w) for j in range(4) if 0 <= q - pat_off(p, j) < kh}
+            for q in range(n_w):
+                if q not in used:
+                    continue
+                L.append(f"ld.shared.f32 sl{q}, [sa+{q * row_bytes}];")
+                L.append(f"ld.shared.f32 sh{q}, [sa+{(q + kh) * row_bytes}];")
+                L.append(f"mov.b64 sW{q}, {{sl{q}, sh{q}}};")
+                for j in range(4):
+                    m = q - pat_off(p, j)
+                    if 0 <= m < kh:
+                        a = j * kh + m
+                        L.append(f"add.rn.f32x2 %{a}, %{a}, sW{q};")
+        elif stream:
             loaded = set()
             for q in range(n_w):
                 for r in (q, q + kh):
@@ -319,6 +351,8 @@ def item_loop(ky, frames, row_bytes, stages, warps, wait_ns=2000000000, stream=T
 ITEMS = ((16, 16, 160, 2, 16), (16, 16, 160, 2, 8), (16, 12, 160, 3, 8),
          (16, 8, 160, 4, 8), (16, 8, 160, 4, 16))  # (KY, F, row bytes, S, consumer warps)
 ITEMS_WINDOW = ()
+# single-use loads (no register copies for the pairs; measured no faster)
+ITEMS_SINGLE = ()
 
 
 def render():
@@ -366,6 +400,12 @@ def render():
     for ky, frames, row_bytes, stages, warps in ITEMS:
         lines, n_acc = item_loop(ky, frames, row_bytes, stages, warps)
         out.append(f"#define ST_ITEM_KY{ky}_F{frames}_R{row_bytes}_S{stages}_W{warps} \\")
+        for ln in lines:
+            out.append(f'  "{ln}\\n\\t" \\')
+        out.append("")
+    for ky, frames, row_bytes, stages, warps in ITEMS_SINGLE:
+        lines, n_acc = item_loop(ky, frames, row_bytes, stages, warps, single_use=True)
+        out.append(f"#define ST_ITEMU_KY{ky}_F{frames}_R{row_bytes}_S{stages}_W{warps} \\")
         for ln in lines:
             out.append(f'  "{ln}\\n\\t" \\')
         out.append("")

@@ -1257,7 +1257,12 @@ int fast_autotune(const FieldDev& fd, FastPlan* fp, int64_t items, Pending* pend
   cudaEventDestroy(e1);
   return launches;
 }
-const char* fast_variant_name(int v) { return v >= 0 && v < kNumVariants ? kVarF32[v].name : "?"; }
+const char* fast_variant_name(const FastPlan* fp, int storage) {
+  int n = 0;
+  const Variant* vars = variants_for(storage, fp && fp->bl, &n);
+  const int v = fp ? fp->variant : -1;
+  return v >= 0 && v < n ? vars[v].name : "?";
+}
 void fast_set_variant(FastPlan* fp, int v) {
   if (fp && v >= 0 && v < kNumVariants) fp->variant = v;
 }

@@ -891,6 +891,14 @@ int32_t st_last_stack_variant(const st_plan_t* p, int32_t field) {
   return p->F[field].last_variant;
 }
 
+const char* st_stack_variant_name(const st_plan_t* p, int32_t field) {
+  if (!p || field < 0 || field >= (int)p->F.size()) return "?";
+  const FieldPlan& fp = p->F[field];
+  if (fp.last_variant == 0) return "direct-gather";
+  if (fp.last_variant != 1 || !fp.fast) return "?";
+  return fast_variant_name(fp.fast, p->o.storage);
+}
+
 st_status st_last_stack_kernel_time(const st_plan_t* p, double* ms, int64_t* launches) {
   if (!p || !ms || !launches) return fail(ST_ERR_INVALID, "NULL argument");
   *ms = p->stack_ms;

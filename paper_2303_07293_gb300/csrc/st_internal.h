@@ -82,7 +82,7 @@ int fast_num_variants_for(const FastPlan* fp, int storage);
 int fast_get_variant(const FastPlan* fp);
 int fast_autotune(const FieldDev& fd, FastPlan* fp, int64_t items, Pending* pend,
                   int64_t pend_cap, Counters* ctr, cudaStream_t s);
-const char* fast_variant_name(int v);
+const char* fast_variant_name(const FastPlan* fp, int storage);
 void fast_set_variant(FastPlan* fp, int v);
 // Whether the field can use the fast kernel at all (width a multiple of
 // 16 bytes for the tensor map).
