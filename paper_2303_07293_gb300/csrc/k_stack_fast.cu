@@ -260,22 +260,6 @@ __device__ __forceinline__ void add_pattern(float2 (&acc)[kMB][KY / 2],
   add_pair_column<KY, pat_off(ID, 3)>(acc[3], pw);
 }
 
-// The body of pattern id in [B, B + 2^L) by L levels of branches on the bits
-// of id (uniform across the block: every warp sees the same id); id kPatterns
-// is a padding frame (no adds).
-template <int KY, int L, int B>
-__device__ __forceinline__ void dispatch_tree(int id, float2 (&acc)[kMB][KY / 2],
-                                              const float2 (&pw)[KY / 2 + 3]) {
-  if constexpr (L == 0) {
-    if constexpr (B < kPatterns) add_pattern<KY, B>(acc, pw);
-  } else {
-    if (id & (1 << (L - 1)))
-      dispatch_tree<KY, L - 1, B + (1 << (L - 1))>(id, acc, pw);
-    else
-      dispatch_tree<KY, L - 1, B>(id, acc, pw);
-  }
-}
-
 // Column pairs: the thread's two columns (c and c + 32) share every row
 // offset, so window row r of both is one register pair and every add is a
 // paired add: acc[j][r] += (wA[r + c_j], wB[r + c_j]).
@@ -400,9 +384,10 @@ __device__ __forceinline__ void tmap_acquire(const CUtensorMap* m) {
 // item's count of fully-inside frames in shared memory.  Warps 0..7 consume.
 // A ring of S stages runs continuously across items and fields; when the
 // work runs out the producer publishes an end item.  Every wait is bounded.
-// OPT (nearest sampling): bit 0 dispatches the frame's pattern by a binary
-// tree of uniform branches on its bits instead of a switch; bit 1 unrolls the
-// frames of a stage.
+// OPT (nearest FP32 sampling): bit 4 runs every stage of an item in one
+// generated PTX block (st_bodies.inc): per frame, the warp's word from the
+// producer and an indexed branch into the pattern's body.  Otherwise a
+// switch on the pattern id selects a C++ body.
 // H: halves per CTA.  With H = 2 the CTA has 16 consumer warps and one
 // producer (one CTA per SM, 112 registers a thread): an item covers two
 // x-velocity tiles, each with its own box per frame and its own 8 warps.
@@ -420,17 +405,17 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
   constexpr int kOut = kMB * KY * (CP ? 2 : 1);  // outputs per thread per item
   constexpr int kItemSlots = 8;
   constexpr int kNoop = kPatterns;  // pattern id of a padding frame
-  static_assert(F <= 4 || (OPT & 24) != 0, "pattern ids of a stage are packed into one word");
+  static_assert(F <= 4 || (OPT & 16) != 0, "pattern ids of a stage are packed into one word");
   extern __shared__ __align__(128) float smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[S];
   __shared__ __align__(8) uint64_t empty_bar[S];
   __shared__ __align__(16) uint32_t slot_ocol[S * H * F];  // packed 4-bit column offsets of 8 warps
   __shared__ uint32_t slot_ids[S];          // packed 8-bit pattern ids of the stage's frames
-  // OPT bit 3 (lean stage loop): per stage, warp and frame, the byte offset of
-  // the warp's window in the ring with the pattern id in the top byte
-  constexpr bool kLean = (OPT & 24) != 0;
-  // OPT bit 4: the whole item's stages (waits, frames, releases) in one PTX block
+  // OPT bit 4: the whole item's stages (waits, frames, releases) in one PTX
+  // block, fed per stage, warp and frame with the byte offset of the warp's
+  // window in the ring and the pattern id in the top byte
   constexpr bool kItemPtx = (OPT & 16) != 0;
+  constexpr bool kLean = kItemPtx;
   __shared__ __align__(16) uint32_t slot_word[kLean ? S * kCW * F : 1];
   __shared__ float slot_fx[BL ? S * F * kXV : 1];  // bilinear: x-fraction of each warp
   __shared__ float4 slot_fy[BL ? S * F : 1];       // bilinear: y-fractions of the 4 y-velocities
@@ -651,9 +636,8 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
     for (int j = 0; j < kMB; ++j)
 #pragma unroll
       for (int m = 0; m < kAccN; ++m) acc[j][m] = make_float2(0.0f, 0.0f);
-    // OPT bit 2: the accumulators as 64-bit register pairs for the PTX bodies
-    constexpr bool kPtx = (OPT & 4) != 0;
-    constexpr bool kAcc64 = kPtx || kLean;
+    // the accumulators as 64-bit register pairs for the PTX block
+    constexpr bool kAcc64 = kItemPtx;
     unsigned long long acc64[kAcc64 ? kMB * kAccN : 1];
 #pragma unroll
     for (int a = 0; a < (kAcc64 ? kMB * kAccN : 1); ++a) acc64[a] = 0ull;
@@ -701,20 +685,6 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
         ok = false;
         break;
       }
-      if constexpr (kLean && !kItemPtx) {
-        static_assert(KY == 16 && F == 4 && !CP && !BL && sizeof(T) == 4,
-                      "the lean stage loop is generated for FP32, KY = 16, F = 4");
-        const uint32_t wb = smem_u32(&slot_word[(c_slot * kCW + warp) * F]);
-        const uint32_t lb = smem_u32(smem) + lane * (uint32_t)sizeof(T);
-        asm volatile(ST_STAGE_KY16_F4_R160 ST_STAGE_OPERANDS_KY16(acc64, wb, lb));
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty_bar[c_slot]);
-        if (++c_slot == S) {
-          c_slot = 0;
-          c_ph ^= 1u;
-        }
-        continue;
-      }
       const uint32_t idw = slot_ids[c_slot];  // the stage's pattern ids
       const T* stage = smem + (size_t)(c_slot * F * H + hw) * box_floats + lane;
       // this warp's column offsets of the stage's frames, 4 bits each, from
@@ -729,7 +699,7 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
         for (int fi = 0; fi < F; ++fi)
           ocw |= ((slot_ocol[(c_slot * H + hw) * F + fi] >> (4 * xw)) & 15u) << (4 * fi);
       }
-#pragma unroll((OPT & 2) ? F : 1)
+#pragma unroll 1
       for (int fi = 0; fi < F; ++fi) {
         const int id = (idw >> (8 * fi)) & 0xffu;
         const T* col = stage + fi * H * box_floats + ((ocw >> (4 * fi)) & 15u);
@@ -810,17 +780,7 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty_bar[c_slot]);
           }
-          if constexpr (kPtx) {
-            static_assert(KY == 16 && !CP && !BL, "PTX bodies are generated for KY = 16");
-            unsigned long long pw64[KY / 2 + 3];
-#pragma unroll
-            for (int q = 0; q < KY / 2 + 3; ++q)
-              asm("mov.b64 %0, {%1, %2};" : "=l"(pw64[q]) : "f"(pw[q].x), "f"(pw[q].y));
-            const unsigned idu = (unsigned)id & 15u;
-            asm(ST_BODY_KY16 ST_BODY_OPERANDS_KY16(acc64, pw64, idu));
-          } else if constexpr ((OPT & 1) != 0) {
-            dispatch_tree<KY, 4, 0>(id, acc, pw);
-          } else switch (id) {
+          switch (id) {
             case 0: add_pattern<KY, 0>(acc, pw); break;
             case 1: add_pattern<KY, 1>(acc, pw); break;
             case 2: add_pattern<KY, 2>(acc, pw); break;
@@ -1079,10 +1039,9 @@ struct Variant {
         #T "_ky" #KY "_s" #S "_f" #F "_cp" #CP "_o" #OPT "_h" #H                                \
   }
 #define NEAR(T, KY, S, F) ST_VARIANT(T, KY, S, F, false, false, 0, 1)
-#define NEARO(T, KY, S, F, OPT) ST_VARIANT(T, KY, S, F, false, false, OPT, 1)
-#define NEARH(T, KY, S, F, OPT) ST_VARIANT(T, KY, S, F, false, false, OPT, 2)
 // the whole item's stages in one PTX block, pattern bodies that load the
-// window rows as they add them (FP32, KY = 16, F = 4)
+// window rows as they add them (FP32, KY = 16); ITEMH: two x-velocity tiles
+// per item, one CTA of 16 consumer warps and a producer per SM
 #define ITEM(T, KY, S, F) ST_VARIANT(T, KY, S, F, false, false, 16, 1)
 #define ITEMH(T, KY, S, F) ST_VARIANT(T, KY, S, F, false, false, 16, 2)
 #define PAIR(T, KY, S, F) ST_VARIANT(T, KY, S, F, false, true, 0, 1)
@@ -1099,8 +1058,6 @@ const Variant kVarBlF32[] = {BILI(float, 8, 8, 4), BILI(float, 12, 8, 4), BILI(f
 const Variant kVarBlF16[] = {BILI(__half, 8, 8, 4), BILI(__half, 12, 8, 4)};
 const Variant kVarBlBF16[] = {BILI(__nv_bfloat16, 8, 8, 4), BILI(__nv_bfloat16, 12, 8, 4)};
 #undef NEAR
-#undef NEARO
-#undef NEARH
 #undef ITEM
 #undef ITEMH
 #undef PAIR

@@ -43,22 +43,32 @@ def test_patterns_are_the_15_monotone_staircases():
 
 def test_item_loop_bodies_add_window_pair_m_plus_c():
     g = _gen()
-    lines, n_acc = g.item_loop(16, 4, 160, 8, 8, stream=False)
-    text = "\n".join(lines)
     kh = 8
-    for p in range(15):
-        body = text.split(f"BT{p}:\n", 1)[1].split("bra.uni SNEXT;", 1)[0]
-        adds = re.findall(r"add\.rn\.f32x2 %(\d+), %(\d+), sW(\d+);", body)
-        assert len(adds) == 4 * kh
-        seen = set()
-        for d, a, w in adds:
-            d, a, w = int(d), int(a), int(w)
-            j, m = divmod(d, kh)
-            assert d == a and w == m + g.pat_off(p, j)
-            seen.add(d)
-        assert seen == set(range(n_acc))
-    # window pair q holds rows q and q + 8 loaded from row offset r * 160 bytes
-    for q in range(kh + 3):
-        assert f"mov.b64 sW{q}, {{sv{q}, sv{q + kh}}};" in text
-    for r in range(16 + 3):
-        assert f"ld.shared.f32 sv{r}, [sa+{r * 160}];" in text
+    for ky, frames, row_bytes, stages, warps in g.ITEMS:
+        lines, n_acc = g.item_loop(ky, frames, row_bytes, stages, warps)
+        text = "\n".join(lines)
+        for p in range(15):
+            body = text.split(f"BT{p}:\n", 1)[1].split("bra.uni SNEXT;", 1)[0]
+            rows, pairs, seen = {}, {}, set()
+            for ln in body.splitlines():
+                mld = re.fullmatch(r"ld\.shared\.f32 sv(\d+), \[sa\+(\d+)\];", ln)
+                mmv = re.fullmatch(r"mov\.b64 sW(\d+), \{sv(\d+), sv(\d+)\};", ln)
+                madd = re.fullmatch(r"add\.rn\.f32x2 %(\d+), %(\d+), sW(\d+);", ln)
+                if mld:
+                    r = int(mld.group(1))
+                    assert int(mld.group(2)) == r * row_bytes and r not in rows
+                    rows[r] = True
+                elif mmv:
+                    q, lo, hi = map(int, mmv.groups())
+                    # the pair holds window rows q and q + 8, both loaded before
+                    assert (lo, hi) == (q, q + kh) and lo in rows and hi in rows
+                    pairs[q] = True
+                elif madd:
+                    d, a, w = map(int, madd.groups())
+                    j, m = divmod(d, kh)
+                    assert d == a and w in pairs and w == m + g.pat_off(p, j)
+                    assert d not in seen
+                    seen.add(d)
+            # every accumulator pair gets exactly one add per frame
+            assert seen == set(range(n_acc))
+        assert text.count("brx.idx.uni sid, BTT;") == 1
