@@ -102,6 +102,8 @@ def parse():
     ap.add_argument("--precision", action="store_true",
                     help="after timing: stack error vs the FP64 oracle at sampled candidates "
                          "and recovery of the injected movers (single-field workloads)")
+    ap.add_argument("--optimizer", default="adam", choices=["adam", "gn"],
+                    help="refine workload: Adam or damped Gauss-Newton steps")
     ap.add_argument("--tile", type=int, default=-1,
                     help="-1 autotune (first warm-up step), 0 default, 1 direct-gather, 2.. variant")
     args = ap.parse_args()
@@ -347,7 +349,7 @@ def bench_refine(args, d, config, dev, world, rank, local):
     cands = torch.from_numpy(np.ascontiguousarray(top).view(np.int32).reshape(-1, 7)).to(dev)
 
     def step():
-        return plan.refine(cands, steps=REFINE_STEPS)
+        return plan.refine(cands, steps=REFINE_STEPS, optimizer=args.optimizer)
 
     for _ in range(args.warmup):
         rec = step()
@@ -376,7 +378,7 @@ def bench_refine(args, d, config, dev, world, rank, local):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         dc = hc.to(dev, non_blocking=True)
-        rec = plan.refine(dc, steps=REFINE_STEPS)
+        rec = plan.refine(dc, steps=REFINE_STEPS, optimizer=args.optimizer)
     te = (time.perf_counter() - t0) / args.steps
     if rank != 0:
         return
@@ -403,8 +405,8 @@ def bench_refine(args, d, config, dev, world, rank, local):
             "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz",
             "footprint_gbs": gbs, "footprint_frac_of_hbm": gbs / hbm,
             "bytes_per_call": bytes_call}
-    cfg = dict(config, candidates=REFINE_N, cutout=REFINE_CUT, adam_steps=REFINE_STEPS,
-               frames=N, storage=args.storage)
+    cfg = dict(config, candidates=REFINE_N, cutout=REFINE_CUT, steps=REFINE_STEPS,
+               optimizer=args.optimizer, frames=N, storage=args.storage)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         import io

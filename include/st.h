@@ -198,17 +198,24 @@ st_status st_stack_search_host(st_plan_t* plan, const float* const* h_frames,
  *     J = F*<g, S_theta> - 0.5*F^2*N*<g, g>,
  * with S_theta the bilinear stack of the raw cube (FP32 input frames of the
  * plan's last search, normalised when the plan normalises) and g a Gaussian
- * of the given FWHM centred on (x0, y0).  `steps` optimiser steps
- * (optimizer 0 = Adam, lr_pos px for x0, y0 and lr_vel for vx, vy) maximise J.
+ * of the given FWHM centred on (x0, y0).  `steps` optimiser steps maximise J,
+ * each with F first set to its optimum <g,S>/(N<g,g>):
+ *   optimizer 0 = Adam, learning rate lr_pos px for x0, y0 and lr_vel for
+ *                 vx, vy;
+ *   optimizer 1 = Gauss-Newton: (vx, vy, x0, y0) move by the solution of
+ *                 (Hs + lr_pos * diag(Hs)) delta = dJ/d(vx, vy, x0, y0), Hs
+ *                 the model's J^T J with F profiled out (Schur complement),
+ *                 lr_pos >= 0 the damping; lr_vel is not used.
+ * The frames' shifts v*(t_i - t_ref) are formed in FP64.
  * d_in: device candidates; d_out: device results [n]; d_grad_out: optional
  * device [n][5] gradient dJ/dtheta at the final parameters (order vx, vy, x0,
  * y0, F).  Requires a prior st_stack_search on the plan (frames resident).
  * The frames are staged per candidate by TMA tile copies: returns
  * ST_ERR_UNSUPPORTED when a field's row (width x element size) is not a
  * multiple of 16 bytes, it has more than 8192 frames or n exceeds 2^31 - 1
- * (one thread block per candidate), and ST_ERR_TIMEOUT
- * when a copy does not land within 2 s (the kernel exits cleanly).
- * Synchronises the plan's stream. */
+ * (one thread block per candidate), ST_ERR_INVALID for another optimizer or
+ * a negative damping, and ST_ERR_TIMEOUT when a copy does not land within
+ * 2 s (the kernel exits cleanly).  Synchronises the plan's stream. */
 st_status st_refine(st_plan_t* plan, const st_candidate* d_in, int64_t n,
                     int32_t steps, int32_t optimizer, float fwhm, float lr_pos,
                     float lr_vel, st_refined* d_out, float* d_grad_out);

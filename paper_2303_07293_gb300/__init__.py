@@ -243,18 +243,25 @@ class Plan:
         return S, Cv
 
     # ------------------------------------------------------------ refinement
-    def refine(self, cands, n=None, steps=20, fwhm=3.0, lr_pos=0.05, lr_vel=None, grad=False):
-        """st_refine: Adam refinement of candidates (device tensor [n, 7] int32 as
-        returned by search).  Returns the refined records (numpy) and, if grad,
-        dJ/dtheta [n, 5] at the final parameters."""
+    def refine(self, cands, n=None, steps=20, fwhm=3.0, lr_pos=0.05, lr_vel=None, grad=False,
+               optimizer="adam", damping=1.0):
+        """st_refine: refinement of candidates (device tensor [n, 7] int32 as
+        returned by search) by Adam (lr_pos, lr_vel) or Gauss-Newton
+        (optimizer="gn", damping).  Returns the refined records (numpy) and,
+        if grad, dJ/dtheta [n, 5] at the final parameters."""
         import torch
         n = cands.shape[0] if n is None else n
-        if lr_vel is None:
+        if optimizer not in ("adam", "gn"):
+            raise ValueError("optimizer must be 'adam' or 'gn'")
+        opt = 1 if optimizer == "gn" else 0
+        if opt == 1:
+            lr_pos, lr_vel = damping, 0.0
+        elif lr_vel is None:
             lr_vel = 0.05 * float(self.fields[0]["dvx"])
         out = torch.empty((max(n, 1), 8), dtype=torch.int32, device=cands.device)
         g = torch.empty((max(n, 1), 5), dtype=torch.float32, device=cands.device) if grad else None
-        _check(lib().st_refine(self._h, _ptr(cands), n, steps, 0, fwhm, lr_pos, lr_vel, _ptr(out),
-                               _ptr(g) if grad else None))
+        _check(lib().st_refine(self._h, _ptr(cands), n, steps, opt, fwhm, lr_pos, lr_vel,
+                               _ptr(out), _ptr(g) if grad else None))
         rec = out[:n].cpu().numpy().view(REFINED_DTYPE).reshape(-1)
         return (rec, g[:n]) if grad else rec
 

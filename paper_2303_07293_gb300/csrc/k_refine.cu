@@ -9,7 +9,18 @@
 // and the adjoint: dJ/dF = <g,S> - F N <g,g>; dJ/dx0 = F <dg/dx0, S> -
 // F^2 N <g, dg/dx0>; dJ/dvx = F sum_p g(p) sum_i dt_i dB_i/dX (the slope of
 // the bilinear cell).  The samples and their derivatives are recomputed on
-// every evaluation, never stored.
+// every evaluation, never stored.  A frame's shift v dt_i is formed to
+// FP64 accuracy (the time offset held as an FP32 pair, the product with an
+// exact FMA error term) and split into its integer part and FP32 fraction.
+//
+// Optimisers (maximise J with F at its optimum <g,S>/(N <g,g>) each step):
+// Adam on (vx, vy, x0, y0), or Gauss-Newton: J is the log-likelihood of the
+// frames under the model F g(p - (x0, y0) - v dt_i), so -Hessian is replaced
+// by the model's J^T J, whose entries need only template sums over the
+// cutout (<g,g>, <g,Gx>, <g,Gy>, <Gx,Gx>, <Gy,Gy>, <Gx,Gy> with G = dg/dx0,
+// dg/dy0) and sum dt, sum dt^2; F is profiled out by the Schur complement of
+// its entry and (vx, vy, x0, y0) move by the solution of
+// (Hs + damping diag(Hs)) delta = dJ/d(vx, vy, x0, y0).
 //
 // One CTA per candidate.  Every pixel of the cutout shares a frame's shift,
 // so a frame contributes one footprint of 65 x 65 taps; a TMA ring of S
@@ -38,7 +49,7 @@ namespace {
 constexpr int kCut = 64;        // cutout side
 constexpr int kThreads = 256;
 constexpr int kPix = kCut * kCut / kThreads;  // 16 rows of one column per thread
-constexpr int kSums = 8;
+constexpr int kSums = 11;
 constexpr int kBoxW = 72;       // footprint columns: 65 taps + up to 7 of alignment
 constexpr int kBoxH = kCut + 1; // footprint rows
 constexpr uint64_t kWaitNs = 2000000000ull;  // wait limit: 2 s of wall-clock time
@@ -63,7 +74,8 @@ struct RefineArgs {
   int64_t n;
   float inv2s2, inv_s2;
   int steps;
-  float lr_pos, lr_vel;
+  int optimizer;                // 0: Adam, 1: Gauss-Newton (optimise mode)
+  float lr_pos, lr_vel;         // Adam learning rates; Gauss-Newton: lr_pos = damping
   float* J;
   float* snr;
   float* grad;                  // [n][5] or null
@@ -119,10 +131,86 @@ struct Shift {
   int ux, uy;
   float fx, fy;
 };
-__device__ __forceinline__ Shift frame_shift(float vx, float vy, float dt) {
-  const float sxv = vx * dt, syv = vy * dt;
-  const float fxl = floorf(sxv), fyl = floorf(syv);
-  return Shift{(int)fxl, (int)fyl, sxv - fxl, syv - fyl};
+// floor and fraction of v (dt_hi + dt_lo) without FP64 arithmetic: p = fl(v
+// dt_hi) and its exact rounding error (one FMA) plus v dt_lo give the product
+// as p + q to about 2^-46 relative; p - floor(p) is exact below 2^23 px, and
+// the fraction is (p - floor(p)) + q rounded to FP32, moved into [0, 1).
+__device__ __forceinline__ void split_shift(float v, float dt_hi, float dt_lo, int* u, float* f) {
+  const float p = v * dt_hi;
+  const float q = __fmaf_rn(v, dt_lo, __fmaf_rn(v, dt_hi, -p));
+  float fl = floorf(p);
+  float r = (p - fl) + q;
+  if (r < 0.0f) {
+    fl -= 1.0f;
+    r += 1.0f;
+  } else if (r >= 1.0f) {
+    fl += 1.0f;
+    r -= 1.0f;
+  }
+  *u = (int)fl;
+  *f = r;
+}
+__device__ __forceinline__ Shift frame_shift(float vx, float vy, float dt_hi, float dt_lo) {
+  Shift s;
+  split_shift(vx, dt_hi, dt_lo, &s.ux, &s.fx);
+  split_shift(vy, dt_hi, dt_lo, &s.uy, &s.fy);
+  return s;
+}
+
+// Solves the 4 x 4 system A x = b by Gaussian elimination with partial
+// pivoting (FP64, in place).  Returns false for a (near) singular matrix.
+__device__ bool solve4(double (&A)[4][4], double (&b)[4]) {
+  for (int c = 0; c < 4; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < 4; ++r)
+      if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+    if (!(fabs(A[piv][c]) > 1e-300)) return false;
+    if (piv != c) {
+      for (int k = 0; k < 4; ++k) {
+        const double tmp = A[c][k];
+        A[c][k] = A[piv][k];
+        A[piv][k] = tmp;
+      }
+      const double tb = b[c];
+      b[c] = b[piv];
+      b[piv] = tb;
+    }
+    for (int r = c + 1; r < 4; ++r) {
+      const double f = A[r][c] / A[c][c];
+      for (int k = c; k < 4; ++k) A[r][k] -= f * A[c][k];
+      b[r] -= f * b[c];
+    }
+  }
+  for (int c = 3; c >= 0; --c) {
+    double v = b[c];
+    for (int k = c + 1; k < 4; ++k) v -= A[c][k] * b[k];
+    b[c] = v / A[c][c];
+  }
+  return true;
+}
+
+// One Gauss-Newton step of (vx, vy, x0, y0) (in th[0..3]) at flux F from the
+// block sums s (template sums s[1] = <g,g>, s[4] = <g,Gx>, s[5] = <g,Gy>,
+// s[8] = <Gx,Gx>, s[9] = <Gy,Gy>, s[10] = <Gx,Gy>), the gradient gr and the
+// frames' sum dt and sum dt^2.  A singular system leaves th unchanged.
+__device__ void gauss_newton_step(float* th, const float (&s)[kSums], const float (&gr)[5],
+                                  float F, int N, double T1, double T2, float damping) {
+  const double f = F, f2 = f * f, n = N;
+  const double xx = s[8], yy = s[9], xy = s[10], gx = s[4], gy = s[5], gg = s[1];
+  const double H[5][5] = {{f2 * T2 * xx, f2 * T2 * xy, f2 * T1 * xx, f2 * T1 * xy, f * T1 * gx},
+                          {f2 * T2 * xy, f2 * T2 * yy, f2 * T1 * xy, f2 * T1 * yy, f * T1 * gy},
+                          {f2 * T1 * xx, f2 * T1 * xy, f2 * n * xx, f2 * n * xy, f * n * gx},
+                          {f2 * T1 * xy, f2 * T1 * yy, f2 * n * xy, f2 * n * yy, f * n * gy},
+                          {f * T1 * gx, f * T1 * gy, f * n * gx, f * n * gy, n * gg}};
+  if (!(H[4][4] > 0.0)) return;
+  double A[4][4], b[4];
+  for (int a = 0; a < 4; ++a) {
+    for (int c = 0; c < 4; ++c) A[a][c] = H[a][c] - H[a][4] * H[4][c] / H[4][4];
+    b[a] = gr[a];
+  }
+  for (int a = 0; a < 4; ++a) A[a][a] += (double)damping * A[a][a];
+  if (!solve4(A, b)) return;
+  for (int a = 0; a < 4; ++a) th[a] = (float)((double)th[a] + b[a]);
 }
 
 template <typename T, bool OPT>
@@ -134,6 +222,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_refine(RefineArgs a) {
   __shared__ __align__(8) uint64_t full[S];
   __shared__ float sh[(kThreads / 32) * kSums];
   __shared__ float th[5];
+  __shared__ double s_t12[2];   // sum dt, sum dt^2 (Gauss-Newton)
   __shared__ int s_ok;
   unsigned char* ring = dsm_raw + ((128u - (smem_u32(dsm_raw) & 127u)) & 127u);
   const int64_t c = blockIdx.x;
@@ -151,13 +240,45 @@ __global__ void __launch_bounds__(kThreads, 2) k_refine(RefineArgs a) {
   }
   const FieldDev& fd = a.fds[fi];
   const int N = fd.N;
-  float* sdt = reinterpret_cast<float*>(ring + (size_t)S * kBox);  // [N] FP32 time offsets
+  // time offsets dt_i = t_i - t_ref as FP32 pairs: sdt (rounded) + sdt_lo
+  float* sdt = reinterpret_cast<float*>(ring + (size_t)S * kBox);
+  float* sdt_lo = sdt + N;
   const CUtensorMap* map = a.maps + fi;
   const int tid = threadIdx.x;
+  const bool gn = OPT && a.optimizer == 1;
   {
     const double* t = a.times[fi];
     const double t_ref = a.t_ref[fi];
-    for (int j = tid; j < N; j += kThreads) sdt[j] = (float)(t[j] - t_ref);
+    double p1 = 0.0, p2 = 0.0;
+    for (int j = tid; j < N; j += kThreads) {
+      const double d = t[j] - t_ref;
+      sdt[j] = (float)d;
+      sdt_lo[j] = (float)(d - (double)(float)d);
+      p1 += d;
+      p2 += d * d;
+    }
+    if (gn) {
+      // sum dt and sum dt^2 in FP64, fixed-order block reduction
+      for (int d = 16; d > 0; d >>= 1) {
+        p1 += __shfl_down_sync(0xffffffffu, p1, d);
+        p2 += __shfl_down_sync(0xffffffffu, p2, d);
+      }
+      __shared__ double s_p[2 * (kThreads / 32)];
+      if ((tid & 31) == 0) {
+        s_p[2 * (tid >> 5)] = p1;
+        s_p[2 * (tid >> 5) + 1] = p2;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        double a1 = 0.0, a2 = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+          a1 += s_p[2 * w];
+          a2 += s_p[2 * w + 1];
+        }
+        s_t12[0] = a1;
+        s_t12[1] = a2;
+      }
+    }
   }
   if (tid == 0) {
     tma_prefetch_desc(map);
@@ -182,7 +303,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_refine(RefineArgs a) {
   uint32_t q_issued = 0;  // (thread 0) sequence number after the last staged frame
   auto issue = [&](int i, uint32_t q, float vx, float vy) {
     q_issued = q + 1;
-    const Shift f = frame_shift(vx, vy, sdt[i]);
+    const Shift f = frame_shift(vx, vy, sdt[i], sdt_lo[i]);
     const int cu0 = cx - kCut / 2 + f.ux, cv0 = cy - kCut / 2 + f.uy;
     const int bx = cu0 & ~(kAl - 1);  // 16-byte aligned box origin (floor, also below 0)
     const int slot = (int)(q % S);
@@ -220,7 +341,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_refine(RefineArgs a) {
         s_ok = 0;
       }
       const float dt = sdt[i];
-      const Shift f = frame_shift(vx, vy, dt);
+      const Shift f = frame_shift(vx, vy, dt, sdt_lo[i]);
       const int cu0 = cx - kCut / 2 + f.ux;
       const T* box = reinterpret_cast<const T*>(ring + (size_t)slot * kBox) +
                      (size_t)row0 * kBoxW + (cu0 - (cu0 & ~(kAl - 1))) + col;
@@ -265,6 +386,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_refine(RefineArgs a) {
       sums[3] += gy * S_[k];
       sums[4] += g[k] * gx;
       sums[5] += g[k] * gy;
+      sums[8] += gx * gx;
+      sums[9] += gy * gy;
+      sums[10] += gx * gy;
     }
     sums[6] = dvx;
     sums[7] = dvy;
@@ -291,6 +415,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_refine(RefineArgs a) {
           r.field = fi;
           a.out[c] = r;
         }
+      } else if (gn) {
+        gauss_newton_step(th, sums, gr, th[4], N, s_t12[0], s_t12[1], a.lr_pos);
       } else {
         // Adam ascent on (vx, vy, x0, y0)
         const float b1 = 0.9f, b2 = 0.999f;
@@ -332,8 +458,8 @@ int launch_refine(const FieldDev* h_fds, int n_fields, const FieldDev* fds, CUte
                   const double* const* times, const double* t_ref, const double* grid,
                   int storage, bool optimise, const float* theta, const int32_t* centre,
                   const int32_t* field, const st_candidate* cand, int64_t n, int steps,
-                  float fwhm, float lr_pos, float lr_vel, float* J, float* snr, float* grad,
-                  st_refined* out, int* err, cudaStream_t s) {
+                  int optimizer, float fwhm, float lr_pos, float lr_vel, float* J, float* snr,
+                  float* grad, st_refined* out, int* err, cudaStream_t s) {
   if (n <= 0) return 0;
   // tensor maps of the fields' cubes (box: the footprint of one frame)
   std::vector<CUtensorMap> maps(n_fields);
@@ -361,6 +487,7 @@ int launch_refine(const FieldDev* h_fds, int n_fields, const FieldDev* fds, CUte
   a.inv2s2 = (float)(1.0 / (2.0 * sg * sg));
   a.inv_s2 = (float)(1.0 / (sg * sg));
   a.steps = steps;
+  a.optimizer = optimizer;
   a.lr_pos = lr_pos;
   a.lr_vel = lr_vel;
   a.J = J;
@@ -368,7 +495,7 @@ int launch_refine(const FieldDev* h_fds, int n_fields, const FieldDev* fds, CUte
   a.grad = grad;
   a.out = out;
   a.err = err;
-  const size_t dt_bytes = sizeof(float) * (size_t)max_n;
+  const size_t dt_bytes = 2 * sizeof(float) * (size_t)max_n;
 #define ST_REF(T, O)                                                                         \
   do {                                                                                       \
     set_smem_attr<T, O>();                                                                   \

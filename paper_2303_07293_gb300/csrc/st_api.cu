@@ -518,16 +518,16 @@ st_status device_search(st_plan_t* p, const float* const* d_frames, const double
 // The refinement kernel over the fields' cubes of the last search.
 st_status run_refine(st_plan_t* p, bool optimise, const float* theta, const int32_t* centre,
                      const int32_t* field, const st_candidate* cand, int64_t n, int steps,
-                     float fwhm, float lr_pos, float lr_vel, float* J, float* snr, float* grad,
-                     st_refined* out) {
+                     int optimizer, float fwhm, float lr_pos, float lr_vel, float* J, float* snr,
+                     float* grad, st_refined* out) {
   const int nf = (int)p->F.size();
   std::vector<FieldDev> h(nf);
   for (int fi = 0; fi < nf; ++fi)
     h[fi] = field_dev(p->F[fi], p->F[fi].last_frames, fi, p->o.storage);
   CK(cudaMemsetAsync(p->d_rerr, 0, sizeof(int), p->s));
   int l = launch_refine(h.data(), nf, p->d_fds, p->d_maps, p->d_times, p->d_tref, p->d_grid,
-                        h[0].storage, optimise, theta, centre, field, cand, n, steps, fwhm,
-                        lr_pos, lr_vel, J, snr, grad, out, p->d_rerr, p->s);
+                        h[0].storage, optimise, theta, centre, field, cand, n, steps, optimizer,
+                        fwhm, lr_pos, lr_vel, J, snr, grad, out, p->d_rerr, p->s);
   if (l < 0)
     return fail(ST_ERR_UNSUPPORTED, "refinement needs frame rows of a multiple of 16 bytes "
                 "and at most %d frames per field", refine_max_frames());
@@ -914,12 +914,15 @@ st_status st_refine(st_plan_t* p, const st_candidate* d_in, int64_t n, int32_t s
     return fail(ST_ERR_INVALID, "n >= 0, d_in/d_out non-NULL, 0 <= steps <= 100000");
   if (!(fwhm > 0.0f) || !std::isfinite(fwhm) || !std::isfinite(lr_pos) || !std::isfinite(lr_vel))
     return fail(ST_ERR_INVALID, "fwhm > 0 and finite learning rates required");
-  if (optimizer != 0) return fail(ST_ERR_UNSUPPORTED, "only optimizer 0 (Adam) is built");
+  if (optimizer != 0 && optimizer != 1)
+    return fail(ST_ERR_INVALID, "optimizer must be 0 (Adam) or 1 (Gauss-Newton)");
+  if (optimizer == 1 && !(lr_pos >= 0.0f))
+    return fail(ST_ERR_INVALID, "Gauss-Newton damping (lr_pos) must be >= 0");
   if (n > 0x7fffffffll) return fail(ST_ERR_UNSUPPORTED, "at most 2^31 - 1 candidates per call");
   if (!p->has_search) return fail(ST_ERR_INVALID, "st_refine needs a prior st_stack_search");
   if (n == 0) return ST_OK;
-  return run_refine(p, true, nullptr, nullptr, nullptr, d_in, n, steps, fwhm, lr_pos, lr_vel,
-                    nullptr, nullptr, d_grad_out, d_out);
+  return run_refine(p, true, nullptr, nullptr, nullptr, d_in, n, steps, optimizer, fwhm, lr_pos,
+                    lr_vel, nullptr, nullptr, d_grad_out, d_out);
 }
 
 st_status st_refine_eval(st_plan_t* p, const float* d_theta, const int32_t* d_centre,
@@ -932,8 +935,8 @@ st_status st_refine_eval(st_plan_t* p, const float* d_theta, const int32_t* d_ce
   if (n > 0x7fffffffll) return fail(ST_ERR_UNSUPPORTED, "at most 2^31 - 1 candidates per call");
   if (!p->has_search) return fail(ST_ERR_INVALID, "st_refine_eval needs a prior st_stack_search");
   if (n == 0) return ST_OK;
-  return run_refine(p, false, d_theta, d_centre, d_field, nullptr, n, 0, fwhm, 0.0f, 0.0f, d_J,
-                    d_snr, d_grad, nullptr);
+  return run_refine(p, false, d_theta, d_centre, d_field, nullptr, n, 0, 0, fwhm, 0.0f, 0.0f,
+                    d_J, d_snr, d_grad, nullptr);
 }
 
 }  // extern "C"

@@ -132,8 +132,8 @@ int launch_refine(const FieldDev* h_fds, int n_fields, const FieldDev* fds, CUte
                   const double* const* times, const double* t_ref, const double* grid,
                   int storage, bool optimise, const float* theta, const int32_t* centre,
                   const int32_t* field, const st_candidate* cand, int64_t n, int steps,
-                  float fwhm, float lr_pos, float lr_vel, float* J, float* snr, float* grad,
-                  st_refined* out, int* err, cudaStream_t s);
+                  int optimizer, float fwhm, float lr_pos, float lr_vel, float* J, float* snr,
+                  float* grad, st_refined* out, int* err, cudaStream_t s);
 
 // Tracks: links the sorted candidates [n] into components (workspace of
 // link_workspace_bytes(n) bytes); writes up to cap tracks, *n_tracks = all.

@@ -293,9 +293,9 @@ def refine_thetas(d, n, seed=9):
 
 def kink_free(th, dt, margin=KINK_MARGIN):
     """True where no frame's shift v dt (either axis) lies within margin of an
-    integer, so FP32 and FP64 pick the same bilinear cell in every frame (the
-    derivative in v jumps between cells); frames at dt = 0 shift by exactly 0
-    on both sides."""
+    integer, so the kernel (parameters rounded to FP32) and the oracle pick
+    the same bilinear cell in every frame (the derivative in v jumps between
+    cells); frames at dt = 0 shift by exactly 0 on both sides."""
     d = dt[dt != 0]
     ok = np.ones(len(th), bool)
     for ax in (0, 1):
@@ -305,35 +305,14 @@ def kink_free(th, dt, margin=KINK_MARGIN):
     return ok
 
 
-def shift_rounding_sd(th, dt, fwhm=3.0):
-    """Standard deviations of the differences that the FP32 shift makes in J,
-    S/N and the gradient.  The kernel forms v dt in FP32 (dt rounded, then
-    the product), so a sample moves by up to |v dt| 2^-23 per axis.  For
-    unit-variance frames that changes a bilinear sample by the move times a
-    first difference (standard deviation sqrt 2) and a slope by the move
-    times a mixed second difference (standard deviation 2); the cutout
-    weights them by g (sqrt(sum g^2) = sqrt(pi) s), the velocity gradient
-    also by dt_i."""
-    s = fwhm / (2.0 * np.sqrt(2.0 * np.log(2.0)))
-    gn = np.sqrt(np.pi) * s
-    move = (np.abs(th[:, 0:1]) + np.abs(th[:, 1:2])) * np.abs(dt)[None, :] * 2.0 ** -23
-    F = np.maximum(np.abs(th[:, 4]), 1.0)
-    m2 = np.sqrt(np.sum(move ** 2, axis=1))
-    sd_J = F * np.sqrt(2.0) * gn * m2
-    sd_snr = np.sqrt(2.0) * m2 / np.sqrt(len(dt))
-    sd_g = F * 2.0 * gn * np.sqrt(np.sum((np.maximum(np.abs(dt), 1.0)[None, :] * move) ** 2,
-                                         axis=1))
-    return sd_J, sd_snr, sd_g
-
-
 def test_fullsize_refine_eval(st):
     """The refinement objective, S/N and adjoint of 4096 candidates on the
     2048^2 x 300-frame refinement field (the benchmark's batch and cutout),
     128 of them against the FP64 oracle with the small-size bars: J and S/N
     within 2e-4 relative, the gradient within 2e-4 of its largest component
-    where no frame sits within 1e-4 px of a bilinear cell edge; each bar
-    plus six standard deviations of the FP32 shift's effect (shifts reach
-    208 px here, against 5 px in the small-size test)."""
+    where no frame sits within 1e-4 px of a bilinear cell edge.  Shifts
+    reach 208 px here (5 px in the small-size test); the kernel forms them
+    in FP64 like the oracle, so the small-size bars hold unchanged."""
     d = synth.make_field("refine")
     cube = oracle.normalize(d["frames"], cr_clip=CR_CLIP)[0]
     del d["frames"]
@@ -353,12 +332,11 @@ def test_fullsize_refine_eval(st):
                                                                  REFINE_SAMPLE - 32,
                                                                  replace=False))])
     oJ, osnr, og = oracle.refine_eval(cube, t, t_ref, th[idx], ce[idx])
-    sd_J, sd_snr, sd_g = shift_rounding_sd(th[idx], t - t_ref)
-    assert np.all(np.abs(J[idx] - oJ) <= 2e-4 * (np.abs(oJ) + 1.0) + 6.0 * sd_J)
-    assert np.all(np.abs(snr[idx] - osnr) <= 2e-4 * (np.abs(osnr) + 1.0) + 6.0 * sd_snr)
+    assert np.all(np.abs(J[idx] - oJ) <= 2e-4 * (np.abs(oJ) + 1.0))
+    assert np.all(np.abs(snr[idx] - osnr) <= 2e-4 * (np.abs(osnr) + 1.0))
     smooth = kink_free(th[idx], t - t_ref)
     assert smooth.sum() >= REFINE_SAMPLE // 2
-    tol = 2e-4 * (np.abs(og).max(axis=1, keepdims=True) + 1.0) + 6.0 * sd_g[:, None]
+    tol = 2e-4 * (np.abs(og).max(axis=1, keepdims=True) + 1.0)
     assert np.all((np.abs(g[idx] - og) <= tol)[smooth])
 
 
