@@ -23,9 +23,19 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(HERE, "st_bodies.inc")
 N_PATTERNS = 15  # ids 0..14; id 15: no-op
-# (rows per thread, frames per stage, box row bytes, ring stages, consumer warps)
-ITEMS = ((16, 16, 160, 2, 16), (16, 16, 160, 2, 8), (16, 12, 160, 3, 8),
-         (16, 8, 160, 4, 8), (16, 8, 160, 4, 16))
+# storage types: PTX load of one window element and its conversion to FP32
+# (FP16 by cvt; a BF16 value is the upper half of its FP32 value)
+DTYPES = {
+    "f32": ("ld.shared.f32 sv{r}, [sa+{o}];", None),
+    "f16": ("ld.shared.b16 sh{r}, [sa+{o}];", "cvt.f32.f16 sv{r}, sh{r};"),
+    "bf16": ("ld.shared.u16 su{r}, [sa+{o}];", "shl.b32 su{r}, su{r}, 16;\nmov.b32 sv{r}, su{r};"),
+}
+# (rows per thread, frames per stage, box row bytes, ring stages, consumer warps, storage):
+# FP32 boxes are 40 wide (160 B rows), 16-bit boxes 48 wide (96 B rows)
+ITEMS = ((16, 16, 160, 2, 16, "f32"), (16, 16, 160, 2, 8, "f32"), (16, 12, 160, 3, 8, "f32"),
+         (16, 8, 160, 4, 8, "f32"), (16, 8, 160, 4, 16, "f32"),
+         (16, 16, 96, 2, 16, "f16"), (16, 16, 96, 2, 8, "f16"),
+         (16, 16, 96, 2, 16, "bf16"), (16, 16, 96, 2, 8, "bf16"))
 
 
 def pat_off(pid, j):
@@ -40,10 +50,12 @@ def pat_off(pid, j):
     return [s[0] + s[1] + s[2], s[1] + s[2], s[2], 0][j]
 
 
-def pattern_body(p, ky, row_bytes):
+def pattern_body(p, ky, row_bytes, dtype="f32"):
     """PTX of pattern p's body: at step q, load window rows q and q + ky/2
-    (each row once), form W[q] and add it to every accumulator pair
-    m = q - c_j; steps whose pair no y-velocity uses are left out."""
+    (each row once, converted to FP32 for 16-bit storage), form W[q] and add
+    it to every accumulator pair m = q - c_j; steps whose pair no y-velocity
+    uses are left out."""
+    ld, cvt = DTYPES[dtype]
     kh = ky // 2
     used = {q for q in range(kh + 3) for j in range(4) if 0 <= q - pat_off(p, j) < kh}
     loaded = set()
@@ -53,7 +65,9 @@ def pattern_body(p, ky, row_bytes):
             continue
         for r in (q, q + kh):
             if r not in loaded:
-                L.append(f"ld.shared.f32 sv{r}, [sa+{r * row_bytes}];")
+                L.append(ld.format(r=r, o=r * row_bytes))
+                if cvt:
+                    L += cvt.format(r=r).split("\n")
                 loaded.add(r)
         L.append(f"mov.b64 sW{q}, {{sv{q}, sv{q + kh}}};")
         for j in range(4):
@@ -64,7 +78,7 @@ def pattern_body(p, ky, row_bytes):
     return L
 
 
-def item_loop(ky, frames, row_bytes, stages, warps, wait_ns=2000000000):
+def item_loop(ky, frames, row_bytes, stages, warps, dtype="f32", wait_ns=2000000000):
     """Every stage of one item for one warp, as one PTX block: per stage,
     wait on the stage's full barrier (all lanes, bounded by wait_ns of the
     global timer), run its frames (per frame: the warp's word, the byte
@@ -84,8 +98,12 @@ def item_loop(ky, frames, row_bytes, stages, warps, wait_ns=2000000000):
     wstride = warps * frames * 4
     L = ["{",
          ".reg .u32 sfi, sw, sa, sid, swp, sst, sbar, st0, st1;",
-         f".reg .f32 sv<{ky + 3}>;",
-         f".reg .b64 sW<{n_w}>;",
+         f".reg .f32 sv<{ky + 3}>;"]
+    if dtype == "f16":
+        L.append(f".reg .b16 sh<{ky + 3}>;")
+    if dtype == "bf16":
+        L.append(f".reg .u32 su<{ky + 3}>;")
+    L += [f".reg .b64 sW<{n_w}>;",
          ".reg .pred sp, swt, sall, slane, sany;",
          f"mov.u32 %{err}, %laneid;",
          f"setp.eq.u32 slane, %{err}, 0;",
@@ -127,7 +145,7 @@ def item_loop(ky, frames, row_bytes, stages, warps, wait_ns=2000000000):
          "brx.idx.uni sid, BTT;"]
     for p in range(N_PATTERNS):
         L.append(f"BT{p}:")
-        L += pattern_body(p, ky, row_bytes)
+        L += pattern_body(p, ky, row_bytes, dtype)
         L.append("bra.uni SNEXT;")
     L += ["BT15:", "SNEXT:", "add.u32 swp, swp, 4;", "add.u32 sfi, sfi, 1;",
           f"setp.lt.u32 sp, sfi, {frames};", "@sp bra.uni SLOOP;",
@@ -150,9 +168,10 @@ def render():
     out = ["// Generated by gen_bodies.py: the consumer loop of the register-window",
            "// stack kernel (pattern bodies entered by brx.idx).  Do not edit.",
            "#pragma once", ""]
-    for ky, frames, row_bytes, stages, warps in ITEMS:
-        lines, n_acc = item_loop(ky, frames, row_bytes, stages, warps)
-        out.append(f"#define ST_ITEM_KY{ky}_F{frames}_R{row_bytes}_S{stages}_W{warps} \\")
+    for ky, frames, row_bytes, stages, warps, dtype in ITEMS:
+        lines, n_acc = item_loop(ky, frames, row_bytes, stages, warps, dtype)
+        sfx = "" if dtype == "f32" else "_" + dtype.upper()
+        out.append(f"#define ST_ITEM_KY{ky}_F{frames}_R{row_bytes}_S{stages}_W{warps}{sfx} \\")
         for ln in lines:
             out.append(f'  "{ln}\\n\\t" \\')
         out.append("")

@@ -51,6 +51,7 @@
 #include <climits>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <utility>
 
 #include "st_bodies.inc"
@@ -644,7 +645,8 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
 
     bool ok = true;
     if constexpr (kItemPtx) {
-      static_assert(KY == 16 && sizeof(T) == 4, "the item loop is generated for FP32, KY = 16");
+      static_assert(KY == 16, "the item loop is generated for KY = 16");
+      constexpr bool kF32 = sizeof(T) == 4, kF16 = std::is_same<T, __half>::value;
       uint32_t slot = (uint32_t)c_slot, ph = c_ph, err = 0;
       __syncwarp();  // the item description is read before the block
       const uint32_t wb0 = smem_u32(&slot_word[warp * F]);
@@ -653,7 +655,17 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
       const uint32_t nst = (uint32_t)spi, skip = 1u;
 #define ST_ITEM_ASM(NAME) \
   asm volatile(NAME ST_ITEM_OPERANDS_KY16(acc64, slot, ph, err, nst, skip, wb0, lb, fb0, eb0))
-      if constexpr (F == 16 && S == 2 && kCW == 16)
+      if constexpr (!kF32 && F == 16 && S == 2 && kCW == 16 && kF16)
+        ST_ITEM_ASM(ST_ITEM_KY16_F16_R96_S2_W16_F16);
+      else if constexpr (!kF32 && F == 16 && S == 2 && kCW == 8 && kF16)
+        ST_ITEM_ASM(ST_ITEM_KY16_F16_R96_S2_W8_F16);
+      else if constexpr (!kF32 && F == 16 && S == 2 && kCW == 16)
+        ST_ITEM_ASM(ST_ITEM_KY16_F16_R96_S2_W16_BF16);
+      else if constexpr (!kF32 && F == 16 && S == 2 && kCW == 8)
+        ST_ITEM_ASM(ST_ITEM_KY16_F16_R96_S2_W8_BF16);
+      else if constexpr (!kF32)
+        static_assert(F == 0, "no generated 16-bit item loop for these stages and warps");
+      else if constexpr (F == 16 && S == 2 && kCW == 16)
         ST_ITEM_ASM(ST_ITEM_KY16_F16_R160_S2_W16);
       else if constexpr (F == 16 && S == 2 && kCW == 8)
         ST_ITEM_ASM(ST_ITEM_KY16_F16_R160_S2_W8);
@@ -1049,10 +1061,10 @@ struct Variant {
 const Variant kVarF32[] = {ITEMH(float, 16, 2, 16), ITEM(float, 16, 2, 16), ITEM(float, 16, 3, 12),
                            ITEM(float, 16, 4, 8), ITEMH(float, 16, 4, 8), NEAR(float, 16, 8, 4),
                            NEAR(float, 24, 6, 4), PAIR(float, 8, 8, 4)};
-const Variant kVarF16[] = {NEAR(__half, 16, 6, 4), NEAR(__half, 16, 8, 4),
-                           PAIR(__half, 8, 8, 4)};
-const Variant kVarBF16[] = {NEAR(__nv_bfloat16, 16, 6, 4), NEAR(__nv_bfloat16, 16, 8, 4),
-                            PAIR(__nv_bfloat16, 8, 8, 4)};
+const Variant kVarF16[] = {ITEMH(__half, 16, 2, 16), ITEM(__half, 16, 2, 16),
+                           NEAR(__half, 16, 8, 4), PAIR(__half, 8, 8, 4)};
+const Variant kVarBF16[] = {ITEMH(__nv_bfloat16, 16, 2, 16), ITEM(__nv_bfloat16, 16, 2, 16),
+                            NEAR(__nv_bfloat16, 16, 8, 4), PAIR(__nv_bfloat16, 8, 8, 4)};
 // bilinear sampling: two window columns, one shared horizontal interpolation
 const Variant kVarBlF32[] = {BILI(float, 8, 8, 4), BILI(float, 12, 8, 4), BILI(float, 16, 6, 4)};
 const Variant kVarBlF16[] = {BILI(__half, 8, 8, 4), BILI(__half, 12, 8, 4)};

@@ -133,7 +133,7 @@ def test_fast_reduced_storage_bitexact_on_rounded_frames(st, storage):
     ks = np.arange(f["nvx"] * f["nvy"], dtype=np.int32)
     oS, oC = oracle.stack_planes(rounded, t, f, ks, prec="fp32")
     ref = oracle.search(rounded, t, f, prec="fp32")
-    for tile in (0, 2, 3, 4):   # 4: column pairs
+    for tile in (0, 2, 3, 4, 5):   # 2, 3: item loop (16 or 8 warps); 5: column pairs
         with st.Plan(f, storage=storage, tile=tile) as p:
             S, Cv = p.dump_stack(0, dev(fr), t, ks)
             got = p.candidates(dev(fr), t)
