@@ -44,17 +44,35 @@ def test_patterns_are_the_15_monotone_staircases():
 def test_item_loop_bodies_add_window_pair_m_plus_c():
     g = _gen()
     kh = 8
-    for ky, frames, row_bytes, stages, warps in g.ITEMS:
-        lines, n_acc = g.item_loop(ky, frames, row_bytes, stages, warps)
+    for ky, frames, row_bytes, stages, warps, dtype in g.ITEMS:
+        lines, n_acc = g.item_loop(ky, frames, row_bytes, stages, warps, dtype)
         text = "\n".join(lines)
         for p in range(15):
             body = text.split(f"BT{p}:\n", 1)[1].split("bra.uni SNEXT;", 1)[0]
             rows, pairs, seen = {}, {}, set()
             for ln in body.splitlines():
+                # a window row reaches FP32 register sv<r>: loaded as FP32, or
+                # loaded as 16 bits at the same byte offset and then converted
+                # (cvt from FP16; a BF16 value shifted into the upper half)
+                m16 = re.fullmatch(r"ld\.shared\.(?:b16 sh|u16 su)(\d+), \[sa\+(\d+)\];", ln)
+                if m16:
+                    assert dtype != "f32" and int(m16.group(2)) == int(m16.group(1)) * row_bytes
+                    continue
+                mcv = re.fullmatch(r"cvt\.f32\.f16 sv(\d+), sh(\d+);|mov\.b32 sv(\d+), su(\d+);",
+                                   ln)
+                if mcv:
+                    r = int(mcv.group(1) or mcv.group(3))
+                    assert r == int(mcv.group(2) or mcv.group(4)) and r not in rows
+                    rows[r] = True
+                    continue
+                if re.fullmatch(r"shl\.b32 su(\d+), su\1, 16;", ln):
+                    assert dtype == "bf16"
+                    continue
                 mld = re.fullmatch(r"ld\.shared\.f32 sv(\d+), \[sa\+(\d+)\];", ln)
                 mmv = re.fullmatch(r"mov\.b64 sW(\d+), \{sv(\d+), sv(\d+)\};", ln)
                 madd = re.fullmatch(r"add\.rn\.f32x2 %(\d+), %(\d+), sW(\d+);", ln)
                 if mld:
+                    assert dtype == "f32"
                     r = int(mld.group(1))
                     assert int(mld.group(2)) == r * row_bytes and r not in rows
                     rows[r] = True
@@ -71,4 +89,5 @@ def test_item_loop_bodies_add_window_pair_m_plus_c():
                     seen.add(d)
             # every accumulator pair gets exactly one add per frame
             assert seen == set(range(n_acc))
+            assert body.count("add.rn.f32x2") == n_acc
         assert text.count("brx.idx.uni sid, BTT;") == 1
