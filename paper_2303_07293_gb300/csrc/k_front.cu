@@ -11,11 +11,11 @@
 //
 // All three are HBM-bound streams.  The median kernels give each thread one
 // pixel, so a warp reads 32 consecutive pixels of a frame per load
-// (coalesced).  Up to 64 frames the samples stay in registers and a bitonic
-// network sorts them; longer groups keep each pixel's samples in a private
-// shared-memory column (lane = bank, no conflicts), copied asynchronously,
-// and select the middle values in place by quickselect, the untouched copy
-// of the column supplying the subtraction.
+// (coalesced).  Up to 64 frames a sorting network per group size selects the
+// median (k_median_select.cu); longer groups keep each pixel's samples in a
+// private shared-memory column (lane = bank, no conflicts), copied
+// asynchronously, and select the middle values in place by quickselect, the
+// untouched copy of the column supplying the subtraction.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -102,74 +102,6 @@ __global__ void __launch_bounds__(kMedThreads)
   for (int i = 0; i < N; ++i) out[(int64_t)i * P + p] = __fsub_rn(orig[i * kMedThreads + lane], med);
 }
 
-// Groups of at most M frames: the pixel's samples live in registers (masked
-// samples as +inf, which sort last), a bitonic network sorts them with
-// branch-free min/max (no divergence between the lanes), and the middle
-// values are picked by a predicated scan.  The input is read again for the
-// subtraction (in place is safe: each thread reads an element before it
-// writes it).
-// One stage (k = K, j = J) of the bitonic network over v[0..M), then the
-// following stages; every index is a compile-time constant.
-template <int M, int K, int J>
-__device__ __forceinline__ void bitonic(float (&v)[M]) {
-#pragma unroll
-  for (int i = 0; i < M; ++i) {
-    const int l = i ^ J;
-    if (l > i) {
-      const float a = v[i], b = v[l];
-      const float lo = fminf(a, b), hi = fmaxf(a, b);
-      v[i] = (i & K) == 0 ? lo : hi;
-      v[l] = (i & K) == 0 ? hi : lo;
-    }
-  }
-  if constexpr (J > 1) {
-    bitonic<M, K, J / 2>(v);
-  } else if constexpr (K < M) {
-    bitonic<M, 2 * K, K>(v);
-  }
-}
-
-template <int M>
-__global__ void __launch_bounds__(128, 4)
-    k_median_sort(const float* in, int N, int64_t P, float* out, float* __restrict__ median) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= P) return;
-  float v[M];
-  int n = 0;
-#pragma unroll
-  for (int i = 0; i < M; ++i) {
-    const float x = i < N ? in[(int64_t)i * P + p] : __int_as_float(0x7f800000);
-    const bool fin = i < N && isfinite(x);
-    v[i] = fin ? x : __int_as_float(0x7f800000);
-    n += fin;
-  }
-  bitonic<M, 2, 1>(v);  // ascending
-  float med = __int_as_float(0x7fc00000);  // NaN: no finite sample
-  if (n > 0) {
-    // sorted ascending: v[k1] = max of v[0..k1], v[k1 + 1] = min of the rest
-    // (a running max / min keeps every index a compile-time constant)
-    const int k1 = (n - 1) / 2;
-    float a = __int_as_float(0xff800000), b = __int_as_float(0x7f800000);
-#pragma unroll
-    for (int i = 0; i < M; ++i) {
-      a = fmaxf(a, i <= k1 ? v[i] : __int_as_float(0xff800000));
-      b = fminf(b, i > k1 ? v[i] : __int_as_float(0x7f800000));
-    }
-    med = (n & 1) ? a : __fmul_rn(__fadd_rn(a, b), 0.5f);
-  }
-  if (median) median[p] = med;
-  // in chunks of 16 frames, so 16 re-reads are in flight at once
-  for (int i0 = 0; i0 < N; i0 += 16) {
-    float x[16];
-#pragma unroll
-    for (int j = 0; j < 16; ++j)
-      x[j] = i0 + j < N ? in[(int64_t)(i0 + j) * P + p] : 0.0f;
-#pragma unroll
-    for (int j = 0; j < 16; ++j)
-      if (i0 + j < N) out[(int64_t)(i0 + j) * P + p] = __fsub_rn(x[j], med);
-  }
-}
-
 __global__ void k_sum_frames(const float* __restrict__ in, int n_sum, int M, int64_t P,
                              float* __restrict__ out) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -199,15 +131,8 @@ int median_max_frames() { return 768; }  // 2 x 768 x 32 floats = 192 KB of shar
 
 int launch_median_subtract(const float* in, int N, int64_t P, float* out, float* median,
                            cudaStream_t s) {
-  if (N <= 64) {  // samples in registers, sorting network
-    const int64_t blocks = (P + 127) / 128;
-    if (blocks > 0x7fffffff) return -1;
-    if (N <= 32)
-      k_median_sort<32><<<(unsigned)blocks, 128, 0, s>>>(in, N, P, out, median);
-    else
-      k_median_sort<64><<<(unsigned)blocks, 128, 0, s>>>(in, N, P, out, median);
-    return 1;
-  }
+  // up to 64 frames: a sorting network per group size (k_median_select.cu)
+  if (N <= median_select_max_frames()) return launch_median_select(in, N, P, out, median, s);
   const size_t smem = (size_t)2 * N * kMedThreads * sizeof(float);
   static bool attr = false;
   if (!attr) {

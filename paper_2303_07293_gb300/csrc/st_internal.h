@@ -148,6 +148,9 @@ int launch_link_tracks(const st_candidate* c, int64_t n, const FieldDev* fds, co
 // binning.  Each returns the number of launches or -1 if the sizes exceed
 // the launch limits.
 int median_max_frames();
+int median_select_max_frames();
+int launch_median_select(const float* in, int N, int64_t P, float* out, float* median,
+                         cudaStream_t s);
 int launch_median_subtract(const float* in, int N, int64_t P, float* out, float* median,
                            cudaStream_t s);
 int launch_sum_frames(const float* in, int n_sum, int M, int64_t P, float* out, cudaStream_t s);

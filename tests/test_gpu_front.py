@@ -37,12 +37,17 @@ def cube(seed, N, H, W, nan_frac=0.02, dup=False):
     return fr
 
 
-@pytest.mark.parametrize("N,H,W,dup", [(1, 5, 7, False), (2, 9, 33, False), (7, 37, 53, False),
-                                       (32, 11, 13, True), (33, 17, 19, False),
-                                       (50, 64, 96, False), (64, 31, 40, True),
-                                       (257, 16, 24, False), (768, 4, 40, False)])
-def test_median_subtract_bitexact(st, N, H, W, dup):
-    fr = cube(N, N, H, W, dup=dup)
+@pytest.mark.parametrize("N,H,W,dup,nan_frac", [
+    (1, 5, 7, False, 0.02), (2, 9, 33, False, 0.02), (7, 37, 53, False, 0.02),
+    (32, 11, 13, True, 0.02), (33, 17, 19, False, 0.02), (50, 64, 96, False, 0.02),
+    (64, 31, 40, True, 0.02), (257, 16, 24, False, 0.02), (768, 4, 40, False, 0.02),
+    # few or no masked samples (the middle positions of the full column), and
+    # many (masked samples of either parity of count, odd and even N)
+    (50, 64, 96, False, 0.0), (49, 33, 40, False, 0.0), (16, 9, 40, True, 0.0),
+    (64, 16, 40, False, 0.3), (63, 16, 40, True, 0.5), (3, 9, 33, False, 0.4),
+    (60, 8, 64, False, 0.05)])
+def test_median_subtract_bitexact(st, N, H, W, dup, nan_frac):
+    fr = cube(N, N, H, W, nan_frac=nan_frac, dup=dup)
     ref, rmed = front.median_subtract(fr)
     out, med = st.median_subtract(dev(fr), with_median=True)
     torch.cuda.synchronize()
