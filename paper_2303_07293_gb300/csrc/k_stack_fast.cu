@@ -1412,8 +1412,16 @@ static const Variant* stage_maps(const FieldDev* fds, FastPlan* const* fps, int 
   static bool attr_set[2][3][2 * kNumVariants] = {};
   for (int d = 0; d < 2; ++d)
     if (!attr_set[fp0->bl][fds[0].storage][2 * vi + d]) {
-      cudaFuncSetAttribute((const void*)(d ? var.dump_fn : var.fn),
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      // as much dynamic shared memory as the device allows beside the
+      // kernel's static shared memory
+      const void* fn = (const void*)(d ? var.dump_fn : var.fn);
+      int dev = 0, optin = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      cudaFuncAttributes fa{};
+      cudaFuncGetAttributes(&fa, fn);
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           optin - (int)fa.sharedSizeBytes);
       attr_set[fp0->bl][fds[0].storage][2 * vi + d] = true;
     }
   *vi_out = vi;
