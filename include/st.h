@@ -263,7 +263,8 @@ st_status st_stack_search_noalloc(const st_field* field, int32_t mode, const flo
                                   const double* h_times, st_candidate* d_out, int64_t capacity,
                                   int64_t* h_count, void* cuda_stream);
 
-/* Diagnostics used by the tests. */
+/* Diagnostics used by the tests and the benchmark (not part of the search's
+ * interface). */
 
 /* Shift tables of field f for timestamps h_times: h_sx [N][nvx], h_sy [N][nvy]
  * (nearest mode: the rounded shifts; bilinear: floor of the shift) and, if
