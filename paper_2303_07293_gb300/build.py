@@ -26,7 +26,7 @@ def _nvcc():
 def _compile(src, verbose):
     obj = os.path.join(OUT, os.path.basename(src) + ".o")
     deps = [src] + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) \
-        + [os.path.join(HERE, "..", "include", "st.h")]
+        + glob.glob(os.path.join(CSRC, "*.inc")) + [os.path.join(HERE, "..", "include", "st.h")]
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(d) for d in deps):
         return obj, ""
     cmd = [_nvcc()] + NVCC_FLAGS + (["-Xptxas", "-v"] if verbose else []) + \

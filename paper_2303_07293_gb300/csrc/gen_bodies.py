@@ -23,6 +23,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(HERE, "st_bodies.inc")
 N_PATTERNS = 15  # ids 0..14; id 15: no-op
+PRE = 3          # window pairs loaded ahead of the indexed branch
 # storage types: PTX load of one window element and its conversion to FP32
 # (FP16 by cvt; a BF16 value is the upper half of its FP32 value)
 DTYPES = {
@@ -50,7 +51,7 @@ def pat_off(pid, j):
     return [s[0] + s[1] + s[2], s[1] + s[2], s[2], 0][j]
 
 
-def pattern_body(p, ky, row_bytes, dtype="f32"):
+def pattern_body(p, ky, row_bytes, dtype="f32", preloaded=()):
     """PTX of pattern p's body: at step q, load window rows q and q + ky/2
     (each row once, converted to FP32 for 16-bit storage), form W[q] and add
     it to every accumulator pair m = q - c_j; steps whose pair no y-velocity
@@ -58,7 +59,7 @@ def pattern_body(p, ky, row_bytes, dtype="f32"):
     ld, cvt = DTYPES[dtype]
     kh = ky // 2
     used = {q for q in range(kh + 3) for j in range(4) if 0 <= q - pat_off(p, j) < kh}
-    loaded = set()
+    loaded = set(preloaded)
     L = []
     for q in range(kh + 3):
         if q not in used:
@@ -82,9 +83,11 @@ def item_loop(ky, frames, row_bytes, stages, warps, dtype="f32", wait_ns=2000000
     """Every stage of one item for one warp, as one PTX block: per stage,
     wait on the stage's full barrier (all lanes, bounded by wait_ns of the
     global timer), run its frames (per frame: the warp's word, the byte
-    offset of its window in the ring with the pattern id in the top byte;
-    brx.idx into the pattern's body), then lane 0 releases the slot on its
-    empty barrier.  Operands: %0.. the accumulator pairs; then the ring slot
+    offset of its window in the ring with the pattern id in the top byte,
+    read one frame ahead; brx.idx into the pattern's body), then lane 0
+    releases the slot on its empty barrier.  The read ahead of a stage's last
+    frame touches the word after the warp's words (the next warp's, or one
+    word of padding after the last).  Operands: %0.. the accumulator pairs; then the ring slot
     and phase (read-write), an error flag (out: 1 = a wait ran out); then the
     number of stages, whether the first stage's wait is already done, the
     address of this warp's words in slot 0, the lane's base address in the
@@ -97,7 +100,7 @@ def item_loop(ky, frames, row_bytes, stages, warps, dtype="f32", wait_ns=2000000
     nst, skip, wb0, lb, fb0, eb0 = (n_acc + 3 + i for i in range(6))
     wstride = warps * frames * 4
     L = ["{",
-         ".reg .u32 sfi, sw, sa, sid, swp, sst, sbar, st0, st1;",
+         ".reg .u32 sfi, sw, snw, sa, sid, swp, sst, sbar, st0, st1;",
          f".reg .f32 sv<{ky + 3}>;"]
     if dtype == "f16":
         L.append(f".reg .b16 sh<{ky + 3}>;")
@@ -136,18 +139,30 @@ def item_loop(ky, frames, row_bytes, stages, warps, dtype="f32", wait_ns=2000000
          "IRUN:",
          f"mad.lo.u32 swp, %{slot}, {wstride}, %{wb0};",
          "mov.u32 sfi, 0;",
-         "SLOOP:",
+         # the frame's word was read by the previous frame (the first here);
+         # the next frame's word is read before the indexed branch
          "ld.shared.u32 sw, [swp];",
+         "SLOOP:",
          "and.b32 sa, sw, 16777215;",
          f"add.u32 sa, sa, %{lb};",
          "shr.u32 sid, sw, 24;",
-         "BTT: .branchtargets " + ", ".join(f"BT{p}" for p in range(16)) + ";",
-         "brx.idx.uni sid, BTT;"]
+         "ld.shared.u32 snw, [swp+4];"]
+    # rows every pattern uses (window pairs 0..PRE-1: the y-velocity with
+    # offset 0 adds them), loaded before the indexed branch so their latency
+    # overlaps it
+    pre = [r for q in range(PRE) for r in (q, q + kh)]
+    ld, cvt = DTYPES[dtype]
+    for r in pre:
+        L.append(ld.format(r=r, o=r * row_bytes))
+        if cvt:
+            L += cvt.format(r=r).split("\n")
+    L += ["BTT: .branchtargets " + ", ".join(f"BT{p}" for p in range(16)) + ";",
+          "brx.idx.uni sid, BTT;"]
     for p in range(N_PATTERNS):
         L.append(f"BT{p}:")
-        L += pattern_body(p, ky, row_bytes, dtype)
+        L += pattern_body(p, ky, row_bytes, dtype, preloaded=pre)
         L.append("bra.uni SNEXT;")
-    L += ["BT15:", "SNEXT:", "add.u32 swp, swp, 4;", "add.u32 sfi, sfi, 1;",
+    L += ["BT15:", "SNEXT:", "mov.u32 sw, snw;", "add.u32 swp, swp, 4;", "add.u32 sfi, sfi, 1;",
           f"setp.lt.u32 sp, sfi, {frames};", "@sp bra.uni SLOOP;",
           # release the slot (every lane's reads are done), next slot
           "bar.warp.sync 0xffffffff;",

@@ -417,7 +417,8 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
   // window in the ring and the pattern id in the top byte
   constexpr bool kItemPtx = (OPT & 16) != 0;
   constexpr bool kLean = kItemPtx;
-  __shared__ __align__(16) uint32_t slot_word[kLean ? S * kCW * F : 1];
+  // (one word of padding: the PTX loop reads one word ahead)
+  __shared__ __align__(16) uint32_t slot_word[kLean ? S * kCW * F + 4 : 1];
   __shared__ float slot_fx[BL ? S * F * kXV : 1];  // bilinear: x-fraction of each warp
   __shared__ float4 slot_fy[BL ? S * F : 1];       // bilinear: y-fractions of the 4 y-velocities
   __shared__ int item_inside[kItemSlots * H];  // frames of an item half fully inside the frame

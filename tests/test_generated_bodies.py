@@ -47,10 +47,12 @@ def test_item_loop_bodies_add_window_pair_m_plus_c():
     for ky, frames, row_bytes, stages, warps, dtype in g.ITEMS:
         lines, n_acc = g.item_loop(ky, frames, row_bytes, stages, warps, dtype)
         text = "\n".join(lines)
+        # rows loaded ahead of the indexed branch serve every body
+        ahead = text.split("SLOOP:\n", 1)[1].split("BTT:", 1)[0]
         for p in range(15):
             body = text.split(f"BT{p}:\n", 1)[1].split("bra.uni SNEXT;", 1)[0]
             rows, pairs, seen = {}, {}, set()
-            for ln in body.splitlines():
+            for ln in ahead.splitlines() + body.splitlines():
                 # a window row reaches FP32 register sv<r>: loaded as FP32, or
                 # loaded as 16 bits at the same byte offset and then converted
                 # (cvt from FP16; a BF16 value shifted into the upper half)
