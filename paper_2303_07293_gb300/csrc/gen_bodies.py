@@ -19,11 +19,13 @@ Run `python gen_bodies.py` after changing the patterns or the instantiated
 shapes; a CPU test checks that the committed file is this script's output.
 """
 import os
+import re
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(HERE, "st_bodies.inc")
 N_PATTERNS = 15  # ids 0..14; id 15: no-op
 PRE = 3          # window pairs loaded ahead of the indexed branch
+PRE_X2 = 3       # the same, two x-velocities a thread
 # storage types: PTX load of one window element and its conversion to FP32
 # (FP16 by cvt; a BF16 value is the upper half of its FP32 value)
 DTYPES = {
@@ -179,6 +181,90 @@ def item_loop(ky, frames, row_bytes, stages, warps, dtype="f32", wait_ns=2000000
     return L, n_acc
 
 
+# two x-velocities a thread (rows per thread, frames per stage, box row bytes,
+# ring stages, consumer warps): 32 accumulator pairs, as for 16 rows; the
+# boxes of 16 x-velocities are 48 FP32 wide (192 B rows)
+ITEMS_X2 = ((8, 16, 192, 2, 8), (8, 16, 192, 2, 16))
+
+
+def pattern_body_x2(p, ky, row_bytes, same, preloaded=()):
+    """Body of pattern p for a thread with two x-velocities (accumulator pair
+    (x, j, m) is operand x*4*ky/2 + j*ky/2 + m; window pairs (q, q + ky/2)).
+    same: both x-velocities read the window at sa, each pair feeding both
+    velocities' accumulators; otherwise x-velocity 0 reads at sa, then
+    x-velocity 1 at sb."""
+    kh = ky // 2
+    used = {q for q in range(kh + 3) for j in range(4) if 0 <= q - pat_off(p, j) < kh}
+    L = []
+    for x, addr in ((0, "sa"), (1, "sb")):
+        if same and x == 1:
+            break
+        loaded = set(preloaded) if x == 0 else set()
+        for q in range(kh + 3):
+            if q not in used:
+                continue
+            for r in (q, q + kh):
+                if r not in loaded:
+                    L.append(f"ld.shared.f32 sv{r}, [{addr}+{r * row_bytes}];")
+                    loaded.add(r)
+            L.append(f"mov.b64 sW{q}, {{sv{q}, sv{q + kh}}};")
+            for xx in ((0, 1) if same else (x,)):
+                for j in range(4):
+                    m = q - pat_off(p, j)
+                    if 0 <= m < kh:
+                        a = xx * 4 * kh + j * kh + m
+                        L.append(f"add.rn.f32x2 %{a}, %{a}, sW{q};")
+    return L
+
+
+def item_loop_x2(ky, frames, row_bytes, stages, warps, wait_ns=2000000000):
+    """As item_loop, for a thread with two adjacent x-velocities.  A frame's
+    word holds the byte offset of x-velocity 0's window in the ring (bits
+    0..17), x-velocity 1's column offset minus 0's plus 16 (bits 18..22) and
+    the body index (bits 24..28): the pattern id, plus 16 when the two
+    x-velocities read different columns (0..14 and 16..30; 15 and 31: no
+    adds).  When their columns agree (most frames: adjacent velocities round
+    to the same shift) one window feeds both velocities' adds."""
+    kh = ky // 2
+    n_acc = 2 * 4 * kh
+    n_w = kh + 3
+    slot, ph, err = n_acc, n_acc + 1, n_acc + 2
+    nst, skip, wb0, lb, fb0, eb0 = (n_acc + 3 + i for i in range(6))
+    wstride = warps * frames * 4
+    # the stage and barrier logic of the one-velocity loop, with its
+    # operands after the accumulators moved up by the extra 4*kh pairs
+    single, _ = item_loop(ky, frames, row_bytes, stages, warps, wait_ns=wait_ns)
+    base = 4 * kh
+
+    def renum(ln):
+        return re.sub(r"%(\d+)", lambda m_: f"%{int(m_.group(1)) + (n_acc - base)}"
+                      if int(m_.group(1)) >= base else m_.group(0), ln)
+    head = [renum(ln) for ln in single[:single.index("SLOOP:")]]
+    tail = [renum(ln) for ln in single[single.index("SNEXT:"):]]
+    head[1] = head[1].replace("sfi, sw, snw, sa, sid,", "sfi, sw, snw, sa, sb, sd, sid,")
+    pre = [r for q in range(PRE_X2) for r in (q, q + kh)]
+    L = head + ["SLOOP:",
+                "and.b32 sa, sw, 262143;",
+                f"add.u32 sa, sa, %{lb};",
+                "shr.u32 sd, sw, 18;",
+                "and.b32 sd, sd, 31;",
+                "mad.lo.u32 sb, sd, 4, sa;",
+                "sub.u32 sb, sb, 64;",
+                "shr.u32 sid, sw, 24;",
+                "ld.shared.u32 snw, [swp+4];"]
+    for r in pre:
+        L.append(f"ld.shared.f32 sv{r}, [sa+{r * row_bytes}];")
+    L += ["BTT: .branchtargets " + ", ".join(f"BT{p}" for p in range(32)) + ";",
+          "brx.idx.uni sid, BTT;"]
+    for same in (True, False):
+        for p in range(N_PATTERNS):
+            L.append(f"BT{p + (0 if same else 16)}:")
+            L += pattern_body_x2(p, ky, row_bytes, same, preloaded=pre)
+            L.append("bra.uni SNEXT;")
+    L += ["BT15:", "BT31:"] + tail
+    return L, n_acc
+
+
 def render():
     out = ["// Generated by gen_bodies.py: the consumer loop of the register-window",
            "// stack kernel (pattern bodies entered by brx.idx).  Do not edit.",
@@ -187,6 +273,12 @@ def render():
         lines, n_acc = item_loop(ky, frames, row_bytes, stages, warps, dtype)
         sfx = "" if dtype == "f32" else "_" + dtype.upper()
         out.append(f"#define ST_ITEM_KY{ky}_F{frames}_R{row_bytes}_S{stages}_W{warps}{sfx} \\")
+        for ln in lines:
+            out.append(f'  "{ln}\\n\\t" \\')
+        out.append("")
+    for ky, frames, row_bytes, stages, warps in ITEMS_X2:
+        lines, n_acc = item_loop_x2(ky, frames, row_bytes, stages, warps)
+        out.append(f"#define ST_ITEMX2_KY{ky}_F{frames}_R{row_bytes}_S{stages}_W{warps} \\")
         for ln in lines:
             out.append(f'  "{ln}\\n\\t" \\')
         out.append("")

@@ -93,6 +93,10 @@ constexpr int kSuper = 4;        // pixel tiles per super-tile side (L2 locality
 constexpr uint64_t kWaitNs = 2000000000ull;  // wait limit: 2 s of wall-clock time
 constexpr unsigned kProducerSleepNs = 128;  // producer back-off between polls
 constexpr int kPatterns = 15;
+constexpr int kX2Wide = 8;       // extra box columns for 16 x-velocities a half
+// table maxima: column offset in a tile, pattern id, shift spread, column
+// offset in a pair of tiles
+constexpr int kMaxes = 4;
 
 // One field of a launch: geometry, per-frame tile tables and thresholds.
 struct FastField {
@@ -182,6 +186,17 @@ __global__ void k_fast_tables(const int32_t* __restrict__ sx, const int32_t* __r
     }
     xt[idx] = make_int4(xs, (int)packed, mn, mx);
     atomicMax(&maxes[0], om);
+    if ((A & 1) == 0) {
+      // tiles A and A + 1 as one box of 16 x-velocities (two a thread): its
+      // largest column offset from the common aligned origin
+      int mn16 = INT_MAX, mx16 = INT_MIN;
+      for (int j = 0; j < 2 * kXV; ++j) {
+        const int v = sx[(int64_t)i * nvx + min(A * kXV + j, nvx - 1)];
+        mn16 = min(mn16, v);
+        mx16 = max(mx16, v);
+      }
+      atomicMax(&maxes[3], mx16 - (mn16 & ~(align - 1)));
+    }
     atomicMin(&xmin[A], mn);
     atomicMax(&xmax[A], mx);
   } else if (idx < nX + nY) {
@@ -390,20 +405,28 @@ __device__ __forceinline__ void tmap_acquire(const CUtensorMap* m) {
 // producer and an indexed branch into the pattern's body.  Otherwise a
 // switch on the pattern id selects a C++ body.
 // H: halves per CTA.  With H = 2 the CTA has 16 consumer warps and one
-// producer (one CTA per SM, 112 registers a thread): an item covers two
+// producer (one CTA per SM, 96 registers a thread): an item covers two
 // x-velocity tiles, each with its own box per frame and its own 8 warps.
+// OPT bit 5 (FP32, KY = 8, with bit 4): two adjacent x-velocities a thread,
+// so a half covers 16 x-velocities (two tables' tiles, one box 8 columns
+// wider); on the frames where the two velocities' columns agree one window
+// feeds both velocities' adds.
 template <typename T, int KY, int S, int F, bool DUMP, bool BL, bool CP, int OPT, int H>
 __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
   static_assert(!(CP && BL), "column pairs are built for nearest sampling");
   static_assert(H == 1 || !(CP || BL), "two halves are built for single-column nearest sampling");
+  constexpr bool kX2 = (OPT & 32) != 0;
+  constexpr int kXPW = kX2 ? 2 : 1;        // x-velocities per thread
+  static_assert(!kX2 || ((OPT & 16) != 0 && sizeof(T) == 4 && KY == 8 && !BL && !CP),
+                "two x-velocities a thread: FP32 nearest item loop, KY = 8");
   constexpr int kTXv = CP ? 2 * kTX : kTX;  // tile width: one or two columns per lane
-  constexpr int kBoxW = Store<T>::kBoxW + (CP ? kTX : 0);
+  constexpr int kBoxW = Store<T>::kBoxW + (CP ? kTX : 0) + (kX2 ? kX2Wide : 0);
   constexpr int kAccN = CP ? KY : KY / 2;   // paired accumulators per y-velocity
   constexpr int kTY = KY;         // tile height: one row group of KY rows per thread
   constexpr int kBoxH = KY + 3 + (BL ? 1 : 0);  // tile rows + staircase offset (+ lower tap)
   constexpr int kEdge = BL ? 1 : 0;  // a bilinear sample also reads the next column / row
   constexpr int kCW = kXV * H;    // consumer warps
-  constexpr int kOut = kMB * KY * (CP ? 2 : 1);  // outputs per thread per item
+  constexpr int kOut = kMB * KY * (CP ? 2 : 1);  // outputs per thread and x-velocity
   constexpr int kItemSlots = 8;
   constexpr int kNoop = kPatterns;  // pattern id of a padding frame
   static_assert(F <= 4 || (OPT & 16) != 0, "pattern ids of a stage are packed into one word");
@@ -431,6 +454,8 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
   const uint32_t box_bytes = (uint32_t)kBoxH * kBoxW * sizeof(T);
   // one frame's box in elements, padded to 128 bytes (compile-time stride)
   constexpr int box_floats = ((kBoxH * kBoxW * (int)sizeof(T) + 127) & ~127) / (int)sizeof(T);
+  // two x-velocities: a window's ring offset fits the word's 18 bits
+  static_assert(!kX2 || S * F * H * box_floats * (int)sizeof(T) < (1 << 18), "ring too large");
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
@@ -454,16 +479,16 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
     const int fi_l = lane % F, h_l = lane / F;
     int f = 0, acq_f = -1;
     int64_t base = 0;                                  // first item of field f
-    int64_t f_items = items_of(*p.ff[0], KY, kTXv, H);  // items of field f
+    int64_t f_items = items_of(*p.ff[0], KY, kTXv, H * kXPW);  // items of field f
     // the item of work-counter index L (-1: past the end); L only grows
     auto locate = [&](int64_t L) -> Item {
       Item it{-1, 0, 0, 0, 0};
       if (L >= p.n_items) return it;
       while (L >= base + f_items) {
         base += f_items;
-        f_items = items_of(*p.ff[++f], KY, kTXv, H);
+        f_items = items_of(*p.ff[++f], KY, kTXv, H * kXPW);
       }
-      return decode_item(*p.ff[f], f, L - base, KY, kTXv, H);
+      return decode_item(*p.ff[f], f, L - base, KY, kTXv, H * kXPW);
     };
     auto take = [&]() -> int64_t {
       int64_t L = 0;
@@ -490,6 +515,9 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
       unsigned id;
       bool valid;
       float4 f0, f1, fy;
+      // two x-velocities: the second tile's packed offsets, and both tiles'
+      // box origins relative to the common box (bits 0..7 and 8..15)
+      uint32_t oc1, dx;
     };
     auto load_entry = [&](const Item& it, const Geo& g, int st) -> Entry {
       Entry e{};
@@ -501,6 +529,21 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
       if (fr >= g.N) return e;
       e.ye = __ldg(g.yt + (int64_t)fr * g.nB + it.B);
       e.id = g.pat[(int64_t)fr * g.nB + it.B];
+      if constexpr (kX2) {
+        // the half's 16 x-velocities: tiles 2A and 2A + 1 of the table (a
+        // missing second tile repeats the first); one box from the lower
+        // origin (both are multiples of 4 columns: 16-byte aligned)
+        const int A0 = 2 * A, A1 = 2 * A + 1;
+        if (A0 >= g.nA) return e;
+        const int4 x0 = __ldg(g.xt + (int64_t)fr * g.nA + A0);
+        const int4 x1 = A1 < g.nA ? __ldg(g.xt + (int64_t)fr * g.nA + A1) : x0;
+        const int bx = min(x0.x, x1.x);
+        e.xe = make_int4(bx, x0.y, min(x0.z, x1.z), max(x0.w, x1.w));
+        e.oc1 = (uint32_t)x1.y;
+        e.dx = (uint32_t)(x0.x - bx) | ((uint32_t)(x1.x - bx) << 8);
+        e.valid = true;
+        return e;
+      }
       if (A >= g.nA) return e;  // the second half of a field's last tile group
       e.xe = __ldg(g.xt + (int64_t)fr * g.nA + A);
       e.valid = true;
@@ -551,7 +594,34 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
       if (st == 0 && lane == 0) item_info[item % kItemSlots] = it;
       const unsigned copies = __ballot_sync(0xffffffffu, cur.valid);
       if (lane == 0 && copies) mbar_expect_tx(&full_bar[slot], box_bytes * __popc(copies));
-      if constexpr (kLean) {
+      if constexpr (kX2) {
+        // word (frame fi, warp w): the ring offset of the window of the
+        // thread's first x-velocity (16 x-velocities a half, two a warp:
+        // 2 wl and 2 wl + 1, both of table tile wl / 4), the second one's
+        // column offset minus the first's plus 16, and the body index: the
+        // pattern id, plus 16 when the two columns differ (15: no adds)
+        const uint32_t oc0 = (uint32_t)cur.xe.y, oc1 = cur.oc1, dx = cur.dx;
+        const uint32_t idv = cur.valid ? cur.id : (unsigned)kNoop;
+#pragma unroll
+        for (int k = lane; k < F * kCW; k += 32) {
+          const int fi = k / kCW, w = k % kCW, h = w / kXV, wl = w % kXV;
+          const int src = h * F + fi;
+          const uint32_t a0 = __shfl_sync(0xffffffffu, oc0, src);
+          const uint32_t a1 = __shfl_sync(0xffffffffu, oc1, src);
+          const uint32_t d = __shfl_sync(0xffffffffu, dx, src);
+          const uint32_t id = __shfl_sync(0xffffffffu, idv, src);
+          const uint32_t pk = wl < kXV / 2 ? a0 : a1;            // the warp's table tile
+          const uint32_t dg = wl < kXV / 2 ? d & 255u : d >> 8;  // its origin in the box
+          const int i0 = (2 * wl) % kXV;
+          const uint32_t o0 = dg + ((pk >> (4 * i0)) & 15u), o1 = dg + ((pk >> (4 * i0 + 4)) & 15u);
+          const bool noop = id == (unsigned)kNoop;
+          const uint32_t base = (uint32_t)(((slot * F + fi) * H + h) * box_floats * (int)sizeof(T));
+          const uint32_t body = noop ? 15u : id + (o1 != o0 ? 16u : 0u);
+          const uint32_t off = noop ? 0u : o0, del = noop ? 16u : o1 + 16u - o0;
+          slot_word[(slot * kCW + w) * F + fi] =
+              (base + off * (uint32_t)sizeof(T)) | ((del & 31u) << 18) | (body << 24);
+        }
+      } else if constexpr (kLean) {
         // one word per lane: word (frame fi, warp w) of the stage, from the
         // entry of lane h * F + fi (its half's packed column offsets and id)
         const uint32_t ocw = (uint32_t)cur.xe.y;
@@ -633,20 +703,24 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
     const FastField* ffp = p.ff[it.f];
     int N = ffp->N;
     const int spi = (N + F - 1) / F;
-    float2 acc[kMB][kAccN];
+    float2 accx[kXPW][kMB][kAccN];
 #pragma unroll
-    for (int j = 0; j < kMB; ++j)
+    for (int xx = 0; xx < kXPW; ++xx)
 #pragma unroll
-      for (int m = 0; m < kAccN; ++m) acc[j][m] = make_float2(0.0f, 0.0f);
-    // the accumulators as 64-bit register pairs for the PTX block
+      for (int j = 0; j < kMB; ++j)
+#pragma unroll
+        for (int m = 0; m < kAccN; ++m) accx[xx][j][m] = make_float2(0.0f, 0.0f);
+    float2 (&acc)[kMB][kAccN] = accx[0];
+    // the accumulators as 64-bit register pairs for the PTX block (x-velocity
+    // xx, y-velocity j, pair m: xx kMB kAccN + j kAccN + m)
     constexpr bool kAcc64 = kItemPtx;
-    unsigned long long acc64[kAcc64 ? kMB * kAccN : 1];
+    unsigned long long acc64[kAcc64 ? kXPW * kMB * kAccN : 1];
 #pragma unroll
-    for (int a = 0; a < (kAcc64 ? kMB * kAccN : 1); ++a) acc64[a] = 0ull;
+    for (int a = 0; a < (kAcc64 ? kXPW * kMB * kAccN : 1); ++a) acc64[a] = 0ull;
 
     bool ok = true;
     if constexpr (kItemPtx) {
-      static_assert(KY == 16, "the item loop is generated for KY = 16");
+      static_assert(KY == 16 || kX2, "the item loop is generated for KY = 16");
       constexpr bool kF32 = sizeof(T) == 4, kF16 = std::is_same<T, __half>::value;
       uint32_t slot = (uint32_t)c_slot, ph = c_ph, err = 0;
       __syncwarp();  // the item description is read before the block
@@ -656,7 +730,14 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
       const uint32_t nst = (uint32_t)spi, skip = 1u;
 #define ST_ITEM_ASM(NAME) \
   asm volatile(NAME ST_ITEM_OPERANDS_KY16(acc64, slot, ph, err, nst, skip, wb0, lb, fb0, eb0))
-      if constexpr (!kF32 && F == 16 && S == 2 && kCW == 16 && kF16)
+      // (two x-velocities of 8 rows: 32 accumulator pairs, as 16 rows of one)
+      if constexpr (kX2 && F == 16 && S == 2 && kCW == 8)
+        ST_ITEM_ASM(ST_ITEMX2_KY8_F16_R192_S2_W8);
+      else if constexpr (kX2 && F == 16 && S == 2 && kCW == 16)
+        ST_ITEM_ASM(ST_ITEMX2_KY8_F16_R192_S2_W16);
+      else if constexpr (kX2)
+        static_assert(F == 0, "no generated two-velocity item loop for these stages and warps");
+      else if constexpr (!kF32 && F == 16 && S == 2 && kCW == 16 && kF16)
         ST_ITEM_ASM(ST_ITEM_KY16_F16_R96_S2_W16_F16);
       else if constexpr (!kF32 && F == 16 && S == 2 && kCW == 8 && kF16)
         ST_ITEM_ASM(ST_ITEM_KY16_F16_R96_S2_W8_F16);
@@ -822,18 +903,24 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
     if (!ok) break;
     if constexpr (kAcc64) {
 #pragma unroll
-      for (int j = 0; j < kMB; ++j)
+      for (int xx = 0; xx < kXPW; ++xx)
 #pragma unroll
-        for (int m = 0; m < kAccN; ++m)
-          asm("mov.b64 {%0, %1}, %2;" : "=f"(acc[j][m].x), "=f"(acc[j][m].y)
-              : "l"(acc64[j * kAccN + m]));
+        for (int j = 0; j < kMB; ++j)
+#pragma unroll
+          for (int m = 0; m < kAccN; ++m)
+            asm("mov.b64 {%0, %1}, %2;" : "=f"(accx[xx][j][m].x), "=f"(accx[xx][j][m].y)
+                : "l"(acc64[(xx * kMB + j) * kAccN + m]));
     }
 
     // ---- epilogue of the item (its last stage was waited on, so the
     // producer's count is visible)
     const int n_full = item_inside[(item % kItemSlots) * H + hw];
     const int x = it.X0 + lane;
-    const int av = (it.A * H + hw) * kXV + xw;
+#pragma unroll
+    for (int xx = 0; xx < kXPW; ++xx) {
+    float2 (&acc)[kMB][kAccN] = accx[xx];
+    // the thread's x-velocity: x-velocity tile (it.A H + hw) of kXV kXPW
+    const int av = ((it.A * H + hw) * kXV + xw) * kXPW + xx;
     if constexpr (CP) {
       // outputs (j, r, h): y-velocity j, row r, column x + 32 h; value
       // acc[j][r].x (h = 0) or .y (h = 1); bit o = (j KY + r) 2 + h
@@ -999,6 +1086,7 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
         }
       }
     }
+    }  // x-velocities of the thread
     // release the item's count slot: the last warp to finish the item clears
     // it (the producer is at most S stages, fewer than kItemSlots - 1 items,
     // ahead of the slowest warp)
@@ -1041,6 +1129,7 @@ struct Variant {
   int threads, stages, ky, stages_f;
   int tx;  // tile width: 32 (one column per lane) or 64 (column pairs)
   int halves;  // x-velocity tiles per item (boxes per frame)
+  int xpw;     // x-velocities per thread (2: a half holds two table tiles)
   const char* name;
 };
 
@@ -1048,7 +1137,7 @@ struct Variant {
   {                                                                                           \
     kernel_of<T, KY, S, F, false, BL, CP, OPT, H>(),                                          \
         kernel_of<T, KY, S, F, true, BL, CP, OPT, H>(),                                       \
-        32 * (kXV * H + 1), S * F, KY, F, CP ? 2 * kTX : kTX, H,                               \
+        32 * (kXV * H + 1), S * F, KY, F, CP ? 2 * kTX : kTX, H, (OPT & 32) ? 2 : 1,           \
         #T "_ky" #KY "_s" #S "_f" #F "_cp" #CP "_o" #OPT "_h" #H                                \
   }
 #define NEAR(T, KY, S, F) ST_VARIANT(T, KY, S, F, false, false, 0, 1)
@@ -1057,11 +1146,16 @@ struct Variant {
 // per item, one CTA of 16 consumer warps and a producer per SM
 #define ITEM(T, KY, S, F) ST_VARIANT(T, KY, S, F, false, false, 16, 1)
 #define ITEMH(T, KY, S, F) ST_VARIANT(T, KY, S, F, false, false, 16, 2)
+// two adjacent x-velocities a thread (FP32, KY = 8): one window feeds both
+// velocities' adds on the frames where their columns agree
+#define ITEMX(T, KY, S, F) ST_VARIANT(T, KY, S, F, false, false, 48, 1)
+#define ITEMXH(T, KY, S, F) ST_VARIANT(T, KY, S, F, false, false, 48, 2)
 #define PAIR(T, KY, S, F) ST_VARIANT(T, KY, S, F, false, true, 0, 1)
 #define BILI(T, KY, S, F) ST_VARIANT(T, KY, S, F, true, false, 0, 1)
 const Variant kVarF32[] = {ITEMH(float, 16, 2, 16), ITEM(float, 16, 2, 16), ITEM(float, 16, 3, 12),
                            ITEM(float, 16, 4, 8), ITEMH(float, 16, 4, 8), NEAR(float, 16, 8, 4),
-                           NEAR(float, 24, 6, 4), PAIR(float, 8, 8, 4)};
+                           NEAR(float, 24, 6, 4), PAIR(float, 8, 8, 4), ITEMXH(float, 8, 2, 16),
+                           ITEMX(float, 8, 2, 16)};
 const Variant kVarF16[] = {ITEMH(__half, 16, 2, 16), ITEM(__half, 16, 2, 16),
                            NEAR(__half, 16, 8, 4), PAIR(__half, 8, 8, 4)};
 const Variant kVarBF16[] = {ITEMH(__nv_bfloat16, 16, 2, 16), ITEM(__nv_bfloat16, 16, 2, 16),
@@ -1073,6 +1167,8 @@ const Variant kVarBlBF16[] = {BILI(__nv_bfloat16, 8, 8, 4), BILI(__nv_bfloat16, 
 #undef NEAR
 #undef ITEM
 #undef ITEMH
+#undef ITEMX
+#undef ITEMXH
 #undef PAIR
 #undef BILI
 #undef ST_VARIANT
@@ -1094,6 +1190,12 @@ const Variant* variants_for(int storage, bool bl, int* count) {
   ST_LIST(kVarF32);
 }
 #undef ST_LIST
+
+// TMA box width of a variant (elements)
+int box_w_of(const Variant& v, int storage) {
+  return (storage == ST_F32 ? Store<float>::kBoxW : Store<__half>::kBoxW) + (v.tx - kTX) +
+         (v.xpw > 1 ? kX2Wide : 0);
+}
 
 // Fractions of a velocity tile, gathered per frame: fxt[(i nA + A) 8 + w] =
 // fx(i, 8A + w) and fyt[(i nB + B) 4 + j] = fy(i, 4B + j) (clamped to the grid).
@@ -1153,8 +1255,9 @@ struct FastPlan {
   int4* yt = nullptr;
   float* fxt = nullptr;   // bilinear: [N][nA][8] x-fractions
   float* fyt = nullptr;   // bilinear: [N][nB][4] y-fractions
-  int* ranges = nullptr;  // xmin[nA], xmax[nA], ymin[nB], ymax[nB], maxes[2]
+  int* ranges = nullptr;  // xmin[nA], xmax[nA], ymin[nB], ymax[nB], maxes[kMaxes]
   int* h_maxes = nullptr; // pinned
+  bool fits_x2 = false;   // the two-velocity variants' wider boxes hold the motion
   int* cov = nullptr;     // covx [nvx*len], covy [nvy*len], mins/maxes [2*nvx + 2*nvy]
   int cov_len = 0;
   int64_t cov_cap = 0;
@@ -1194,7 +1297,7 @@ int fast_get_variant(const FastPlan* fp) { return fp ? fp->variant : -1; }
 int fast_autotune(const FieldDev& fd, FastPlan* fp, int64_t items, Pending* pend,
                   int64_t pend_cap, Counters* ctr, cudaStream_t s) {
   int n = 0;
-  variants_for(fd.storage, fp->bl, &n);
+  const Variant* vars = variants_for(fd.storage, fp->bl, &n);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -1203,6 +1306,7 @@ int fast_autotune(const FieldDev& fd, FastPlan* fp, int64_t items, Pending* pend
   int launches = 0;
   fp->item_limit = items;
   for (int v = 0; v < n; ++v) {
+    if (vars[v].xpw > 1 && !fp->fits_x2) continue;  // its boxes do not hold the motion
     fp->variant = v;
     float ms_min = 1e30f;
     for (int rep = 0; rep < 2; ++rep) {  // first run warms up
@@ -1230,7 +1334,8 @@ int fast_autotune(const FieldDev& fd, FastPlan* fp, int64_t items, Pending* pend
 const char* fast_variant_name(const FastPlan* fp, int storage) {
   int n = 0;
   const Variant* vars = variants_for(storage, fp && fp->bl, &n);
-  const int v = fp ? fp->variant : -1;
+  int v = fp ? fp->variant : -1;
+  if (v >= 0 && v < n && vars[v].xpw > 1 && !fp->fits_x2) v = 0;  // as the launch runs it
   return v >= 0 && v < n ? vars[v].name : "?";
 }
 void fast_set_variant(FastPlan* fp, int v) {
@@ -1257,8 +1362,8 @@ bool fast_plan_build(const FieldDev& fd, int mode, FastPlan** out) {
               cudaMalloc(&fp->fyt, sizeof(float) * nfy) == cudaSuccess &&
               cudaMalloc(&fp->xt, sizeof(int4) * (size_t)fd.N * fp->nA) == cudaSuccess &&
               cudaMalloc(&fp->yt, sizeof(int4) * (size_t)fd.N * fp->nB) == cudaSuccess &&
-              cudaMalloc(&fp->ranges, sizeof(int) * (2 * fp->nA + 2 * fp->nB + 3)) == cudaSuccess &&
-              cudaMallocHost(&fp->h_maxes, sizeof(int) * 3) == cudaSuccess &&
+              cudaMalloc(&fp->ranges, sizeof(int) * (2 * fp->nA + 2 * fp->nB + kMaxes)) == cudaSuccess &&
+              cudaMallocHost(&fp->h_maxes, sizeof(int) * kMaxes) == cudaSuccess &&
               cudaMalloc(&fp->d_pat, (size_t)fd.N * fp->nB) == cudaSuccess &&
               cudaMalloc(&fp->d_ff, sizeof(FastField)) == cudaSuccess &&
               cudaMalloc(&fp->d_map, sizeof(CUtensorMap)) == cudaSuccess;
@@ -1301,7 +1406,7 @@ int fast_prepare(const FieldDev& fd, FastPlan* fp, cudaStream_t s, bool* fits) {
   cudaMemsetAsync(xmax, 0x80, sizeof(int) * nA, s);
   cudaMemsetAsync(ymin, 0x7f, sizeof(int) * nB, s);
   cudaMemsetAsync(ymax, 0x80, sizeof(int) * nB, s);
-  cudaMemsetAsync(maxes, 0, sizeof(int) * 3, s);
+  cudaMemsetAsync(maxes, 0, sizeof(int) * kMaxes, s);
   int64_t n = (int64_t)fd.N * (nA + nB);
   k_fast_tables<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(fd.sx, fd.sy, fd.N, fd.nvx, fd.nvy, nA,
                                                             nB, fp->xt, fp->yt, xmin, xmax, ymin,
@@ -1314,7 +1419,7 @@ int fast_prepare(const FieldDev& fd, FastPlan* fp, cudaStream_t s, bool* fits) {
   }
   k_shift_spread<<<(fd.nvx + 127) / 128, 128, 0, s>>>(fd.sx, fd.N, fd.nvx, maxes + 2);
   k_shift_spread<<<(fd.nvy + 127) / 128, 128, 0, s>>>(fd.sy, fd.N, fd.nvy, maxes + 2);
-  cudaMemcpyAsync(fp->h_maxes, maxes, sizeof(int) * 3, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(fp->h_maxes, maxes, sizeof(int) * kMaxes, cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return 1;
   // coverage prefix tables: one row per velocity, as long as the widest spread
   const int len = fp->h_maxes[2];
@@ -1377,6 +1482,10 @@ int fast_prepare(const FieldDev& fd, FastPlan* fp, cudaStream_t s, bool* fits) {
                            ? Store<float>::kBoxW - kTX - (fp->bl ? 1 : 0)
                            : Store<__half>::kOColMax;
   *fits = fp->h_maxes[0] <= ocol_max && fp->h_maxes[1] < kPatterns && fd.N >= 8;
+  // two x-velocities a thread: column offsets within the wider box, and below
+  // 16 so the second velocity's offset from the first fits the 5-bit field
+  fp->fits_x2 = *fits && fd.storage == ST_F32 && !fp->bl &&
+                fp->h_maxes[3] <= Store<float>::kBoxW + kX2Wide - kTX - 1;
   return 1;
 }
 
@@ -1389,11 +1498,13 @@ static const Variant* stage_maps(const FieldDev* fds, FastPlan* const* fps, int 
   FastPlan* fp0 = fps[0];
   int nvar = 0;
   const Variant* vars = variants_for(fds[0].storage, fp0->bl, &nvar);
-  const int vi = fp0->variant < nvar ? fp0->variant : 0;
+  int vi = fp0->variant < nvar ? fp0->variant : 0;
+  // a two-velocity variant needs every field's motion within its boxes
+  for (int i = 0; i < n && vars[vi].xpw > 1; ++i)
+    if (!fps[i]->fits_x2) vi = 0;
   const Variant& var = vars[vi];
   const int boxh = var.ky + 3 + (fp0->bl ? 1 : 0);
-  const int boxw = (fds[0].storage == ST_F32 ? Store<float>::kBoxW : Store<__half>::kBoxW) +
-                   (var.tx - kTX);
+  const int boxw = box_w_of(var, fds[0].storage);
   for (int i = 0; i < n; ++i) {
     FastPlan* fp = fps[i];
     if (fds[i].storage != fds[0].storage || fp->bl != fp0->bl) return nullptr;
@@ -1444,8 +1555,7 @@ int launch_stack_fast_multi(const FieldDev* fds, FastPlan* const* fps, int n, fl
   if (!vp) return -1;
   const Variant& var = *vp;
   const int ky = var.ky, boxh = ky + 3 + (fp0->bl ? 1 : 0);
-  const int boxw = (fds[0].storage == ST_F32 ? Store<float>::kBoxW : Store<__half>::kBoxW) +
-                   (var.tx - kTX);
+  const int boxw = box_w_of(var, fds[0].storage);
   // fields longest first (the items of the most frames are taken first)
   int order[kMaxFields];
   for (int i = 0; i < n; ++i) order[i] = i;
@@ -1456,12 +1566,13 @@ int launch_stack_fast_multi(const FieldDev* fds, FastPlan* const* fps, int n, fl
   for (int i = 0; i < n; ++i) {
     a.ff[i] = fps[order[i]]->d_ff;
     a.maps[i] = fps[order[i]]->d_map;
-    total += items_of(fps[order[i]]->h_ff, ky, var.tx, var.halves);
+    total += items_of(fps[order[i]]->h_ff, ky, var.tx, var.halves * var.xpw);
   }
   a.n_fields = n;
-  // an autotuning run covers the same work for every variant (an item of a
-  // two-half variant holds two x-velocity tiles)
-  const int64_t limit = fp0->item_limit > 0 ? (fp0->item_limit + var.halves - 1) / var.halves : 0;
+  // an autotuning run covers the same work for every variant: item_limit
+  // items of 32 x 16 pixels and 8 x-velocities
+  const int64_t unit = (int64_t)var.halves * var.xpw * var.ky * var.tx;  // per 8 x-velocities
+  const int64_t limit = fp0->item_limit > 0 ? (fp0->item_limit * 16 * kTX + unit - 1) / unit : 0;
   a.n_items = limit > 0 && total > limit ? limit : total;
   a.work = &ctr->work_next;
   a.pend = pend;

@@ -93,3 +93,52 @@ def test_item_loop_bodies_add_window_pair_m_plus_c():
             assert seen == set(range(n_acc))
             assert body.count("add.rn.f32x2") == n_acc
         assert text.count("brx.idx.uni sid, BTT;") == 1
+
+
+def test_two_velocity_bodies_add_each_velocitys_window_pair_m_plus_c():
+    # a symbolic run of each body: registers hold (window base, byte offset)
+    # of what they loaded; x-velocity 0's window is at sa, x-velocity 1's at
+    # sa when the body index is below 16 (the two columns agree) and at sb
+    # otherwise; accumulator pair (x, j, m) is operand x*16 + j*4 + m
+    g = _gen()
+    for ky, frames, row_bytes, stages, warps in g.ITEMS_X2:
+        kh = ky // 2
+        lines, n_acc = g.item_loop_x2(ky, frames, row_bytes, stages, warps)
+        assert n_acc == 2 * 4 * kh
+        text = "\n".join(lines)
+        # the word: 18 bits of ring offset, the second column's offset from
+        # the first plus 16 in bits 18..22, the body index from bit 24
+        head = text.split("SLOOP:\n", 1)[1].split("BTT:", 1)[0]
+        for ln in ("and.b32 sa, sw, 262143;", "shr.u32 sd, sw, 18;", "and.b32 sd, sd, 31;",
+                   "mad.lo.u32 sb, sd, 4, sa;", "sub.u32 sb, sb, 64;", "shr.u32 sid, sw, 24;"):
+            assert ln in head.splitlines(), ln
+        targets = text.split("BTT: .branchtargets ", 1)[1].split(";", 1)[0].split(", ")
+        assert targets == [f"BT{b}" for b in range(32)]
+        for b in range(32):
+            body = text.split(f"BT{b}:\n", 1)[1].split("bra.uni SNEXT;", 1)[0]
+            if b in (15, 31):
+                assert body.startswith("BT31:") or body.startswith("SNEXT:")
+                assert "add.rn" not in body.split("SNEXT:", 1)[0]
+                continue
+            p, same = b % 16, b < 16
+            sv, sw, adds = {}, {}, {}
+            for ln in head.splitlines() + body.splitlines():
+                mld = re.fullmatch(r"ld\.shared\.f32 sv(\d+), \[(sa|sb)\+(\d+)\];", ln)
+                mmv = re.fullmatch(r"mov\.b64 sW(\d+), \{sv(\d+), sv(\d+)\};", ln)
+                madd = re.fullmatch(r"add\.rn\.f32x2 %(\d+), %(\d+), sW(\d+);", ln)
+                if mld:
+                    sv[int(mld.group(1))] = (mld.group(2), int(mld.group(3)))
+                elif mmv:
+                    q, lo, hi = map(int, mmv.groups())
+                    sw[q] = (sv[lo], sv[hi])
+                elif madd:
+                    d, a, w = map(int, madd.groups())
+                    assert d == a and d not in adds
+                    adds[d] = sw[w]
+            assert sorted(adds) == list(range(n_acc)), b
+            for d, (lo, hi) in adds.items():
+                x, rest = divmod(d, 4 * kh)
+                j, m = divmod(rest, kh)
+                base = "sa" if (x == 0 or same) else "sb"
+                r = m + g.pat_off(p, j)
+                assert lo == (base, r * row_bytes) and hi == (base, (r + kh) * row_bytes), (b, d)

@@ -25,7 +25,8 @@ def st():
     return m
 
 
-VARIANTS = [0, 2, 3, 4, 5, 6, 7, 8, 9]  # plan default and every FP32 register-window variant
+VARIANTS = [0, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11]  # plan default and every FP32 register-window variant
+X2_TILES = (10, 11)  # two x-velocities a thread (16 or 8 consumer warps)
 
 
 def dev(a):
@@ -56,6 +57,8 @@ def test_fast_dump_bitexact(st, seed, shape):
             S, Cv = p.dump_stack(0, dev(fr), t, ks)
             p.candidates(dev(fr), t)
             assert p.last_stack_variant(0) == 1, "register-window kernel not used"
+            if tile in X2_TILES:   # these fields' motion fits the 16-velocity boxes
+                assert "_o48_" in p.stack_variant_name(0), p.stack_variant_name(0)
         assert np.array_equal(Cv.cpu().numpy(), oC), tile
         assert np.array_equal(S.cpu().numpy(), oS.astype(np.float32)), tile
 
@@ -171,6 +174,20 @@ def test_fast_falls_back_when_motion_spans_exceed_window(st):
         assert p.last_stack_variant(0) == 0
     ref = oracle.search(d["frames"], d["times"], d["field"], prec="fp32")
     assert got[["x", "y", "k"]].tolist() == ref[["x", "y", "k"]].tolist()
+
+
+def test_two_velocity_variant_falls_back_when_its_boxes_are_too_narrow(st):
+    # velocity step 0.45 over |dt| up to about 2: an 8-velocity tile's column
+    # offsets reach 8 (its box's limit), a 16-velocity tile's reach 16 (above
+    # the wider box's limit of 15)
+    fr, t, f = field(15, W=128, H=40, N=24, nvx=24, nvy=6, dv=0.45, span=4.0, ref=12)
+    ref = oracle.search(fr, t, f, prec="fp32")
+    for tile in X2_TILES:
+        with st.Plan(f, tile=tile) as p:
+            got = p.candidates(dev(fr), t)
+            assert p.last_stack_variant(0) == 1, "register-window kernel not used"
+            assert "_o48_" not in p.stack_variant_name(0), p.stack_variant_name(0)
+        assert got[["x", "y", "k", "n_cov"]].tolist() == ref[["x", "y", "k", "n_cov"]].tolist()
 
 
 def test_add_rate_probe(st):
