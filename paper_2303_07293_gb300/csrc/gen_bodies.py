@@ -219,20 +219,19 @@ def pattern_body_x2(p, ky, row_bytes, same, preloaded=()):
 
 def item_loop_x2(ky, frames, row_bytes, stages, warps, wait_ns=2000000000):
     """As item_loop, for a thread with two adjacent x-velocities.  A frame's
-    word holds the byte offset of x-velocity 0's window in the ring (bits
-    0..17), x-velocity 1's column offset minus 0's plus 16 (bits 18..22) and
-    the body index (bits 24..28): the pattern id, plus 16 when the two
-    x-velocities read different columns (0..14 and 16..30; 15 and 31: no
-    adds).  When their columns agree (most frames: adjacent velocities round
-    to the same shift) one window feeds both velocities' adds."""
+    words are four: the body index (the pattern id, plus 16 when the two
+    x-velocities read different columns: 0..14 and 16..30; 15 and 31: no
+    adds), the byte offsets in the ring of x-velocity 0's and x-velocity 1's
+    windows, and one unused word; the next frame's four are read in one
+    vector load before the indexed branch.  When the two columns agree (most
+    frames: adjacent velocities round to the same shift) one window feeds
+    both velocities' adds.  Slot s's words are at words0 + s*warps*frames*16."""
     kh = ky // 2
     n_acc = 2 * 4 * kh
-    n_w = kh + 3
-    slot, ph, err = n_acc, n_acc + 1, n_acc + 2
-    nst, skip, wb0, lb, fb0, eb0 = (n_acc + 3 + i for i in range(6))
-    wstride = warps * frames * 4
+    lb = n_acc + 3 + 3
     # the stage and barrier logic of the one-velocity loop, with its
-    # operands after the accumulators moved up by the extra 4*kh pairs
+    # operands after the accumulators moved up by the extra 4*kh pairs, its
+    # words four times as wide
     single, _ = item_loop(ky, frames, row_bytes, stages, warps, wait_ns=wait_ns)
     base = 4 * kh
 
@@ -241,17 +240,18 @@ def item_loop_x2(ky, frames, row_bytes, stages, warps, wait_ns=2000000000):
                       if int(m_.group(1)) >= base else m_.group(0), ln)
     head = [renum(ln) for ln in single[:single.index("SLOOP:")]]
     tail = [renum(ln) for ln in single[single.index("SNEXT:"):]]
-    head[1] = head[1].replace("sfi, sw, snw, sa, sid,", "sfi, sw, snw, sa, sb, sd, sid,")
+    head[1] = head[1].replace("sfi, sw, snw, sa, sid,", "sfi, sw, sa, sb, sid, sna, snb, snid,")
+    i = head.index("ld.shared.u32 sw, [swp];")
+    head[i:i + 1] = ["ld.shared.v4.u32 {sid, sa, sb, sw}, [swp];",
+                     f"add.u32 sa, sa, %{lb};",
+                     f"add.u32 sb, sb, %{lb};"]
+    i = [k for k, ln in enumerate(head) if ln.startswith("mad.lo.u32 swp,")][0]
+    head[i] = re.sub(r", (\d+), ", lambda m_: f", {int(m_.group(1)) * 4}, ", head[i])
+    i = tail.index("mov.u32 sw, snw;")
+    tail[i:i + 2] = ["mov.u32 sid, snid;", f"add.u32 sa, sna, %{lb};", f"add.u32 sb, snb, %{lb};",
+                     "add.u32 swp, swp, 16;"]
     pre = [r for q in range(PRE_X2) for r in (q, q + kh)]
-    L = head + ["SLOOP:",
-                "and.b32 sa, sw, 262143;",
-                f"add.u32 sa, sa, %{lb};",
-                "shr.u32 sd, sw, 18;",
-                "and.b32 sd, sd, 31;",
-                "mad.lo.u32 sb, sd, 4, sa;",
-                "sub.u32 sb, sb, 64;",
-                "shr.u32 sid, sw, 24;",
-                "ld.shared.u32 snw, [swp+4];"]
+    L = head + ["SLOOP:", "ld.shared.v4.u32 {snid, sna, snb, sw}, [swp+16];"]
     for r in pre:
         L.append(f"ld.shared.f32 sv{r}, [sa+{r * row_bytes}];")
     L += ["BTT: .branchtargets " + ", ".join(f"BT{p}" for p in range(32)) + ";",

@@ -440,8 +440,11 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
   // window in the ring and the pattern id in the top byte
   constexpr bool kItemPtx = (OPT & 16) != 0;
   constexpr bool kLean = kItemPtx;
-  // (one word of padding: the PTX loop reads one word ahead)
-  __shared__ __align__(16) uint32_t slot_word[kLean ? S * kCW * F + 4 : 1];
+  // (four words of padding: the PTX loop reads one frame's words ahead).
+  // Two x-velocities a thread: four words per frame and warp (body index,
+  // the two windows' byte offsets, one unused), read as one vector
+  constexpr int kWords = kX2 ? 4 : 1;
+  __shared__ __align__(16) uint32_t slot_word[kLean ? S * kCW * F * kWords + 4 : 1];
   __shared__ float slot_fx[BL ? S * F * kXV : 1];  // bilinear: x-fraction of each warp
   __shared__ float4 slot_fy[BL ? S * F : 1];       // bilinear: y-fractions of the 4 y-velocities
   __shared__ int item_inside[kItemSlots * H];  // frames of an item half fully inside the frame
@@ -454,8 +457,6 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
   const uint32_t box_bytes = (uint32_t)kBoxH * kBoxW * sizeof(T);
   // one frame's box in elements, padded to 128 bytes (compile-time stride)
   constexpr int box_floats = ((kBoxH * kBoxW * (int)sizeof(T) + 127) & ~127) / (int)sizeof(T);
-  // two x-velocities: a window's ring offset fits the word's 18 bits
-  static_assert(!kX2 || S * F * H * box_floats * (int)sizeof(T) < (1 << 18), "ring too large");
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
@@ -595,11 +596,10 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
       const unsigned copies = __ballot_sync(0xffffffffu, cur.valid);
       if (lane == 0 && copies) mbar_expect_tx(&full_bar[slot], box_bytes * __popc(copies));
       if constexpr (kX2) {
-        // word (frame fi, warp w): the ring offset of the window of the
-        // thread's first x-velocity (16 x-velocities a half, two a warp:
-        // 2 wl and 2 wl + 1, both of table tile wl / 4), the second one's
-        // column offset minus the first's plus 16, and the body index: the
-        // pattern id, plus 16 when the two columns differ (15: no adds)
+        // words (frame fi, warp w): the body index (the pattern id, plus 16
+        // when the two columns differ; 15: no adds) and the ring offsets of
+        // the windows of the thread's two x-velocities (16 x-velocities a
+        // half, two a warp: 2 wl and 2 wl + 1, both of table tile wl / 4)
         const uint32_t oc0 = (uint32_t)cur.xe.y, oc1 = cur.oc1, dx = cur.dx;
         const uint32_t idv = cur.valid ? cur.id : (unsigned)kNoop;
 #pragma unroll
@@ -617,9 +617,9 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
           const bool noop = id == (unsigned)kNoop;
           const uint32_t base = (uint32_t)(((slot * F + fi) * H + h) * box_floats * (int)sizeof(T));
           const uint32_t body = noop ? 15u : id + (o1 != o0 ? 16u : 0u);
-          const uint32_t off = noop ? 0u : o0, del = noop ? 16u : o1 + 16u - o0;
-          slot_word[(slot * kCW + w) * F + fi] =
-              (base + off * (uint32_t)sizeof(T)) | ((del & 31u) << 18) | (body << 24);
+          *reinterpret_cast<uint4*>(&slot_word[((slot * kCW + w) * F + fi) * 4]) =
+              make_uint4(body, base + (noop ? 0u : o0) * (uint32_t)sizeof(T),
+                         base + (noop ? 0u : o1) * (uint32_t)sizeof(T), 0u);
         }
       } else if constexpr (kLean) {
         // one word per lane: word (frame fi, warp w) of the stage, from the
@@ -724,7 +724,7 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
       constexpr bool kF32 = sizeof(T) == 4, kF16 = std::is_same<T, __half>::value;
       uint32_t slot = (uint32_t)c_slot, ph = c_ph, err = 0;
       __syncwarp();  // the item description is read before the block
-      const uint32_t wb0 = smem_u32(&slot_word[warp * F]);
+      const uint32_t wb0 = smem_u32(&slot_word[warp * F * kWords]);
       const uint32_t lb = smem_u32(smem) + lane * (uint32_t)sizeof(T);
       const uint32_t fb0 = smem_u32(&full_bar[0]), eb0 = smem_u32(&empty_bar[0]);
       const uint32_t nst = (uint32_t)spi, skip = 1u;
@@ -1152,10 +1152,12 @@ struct Variant {
 #define ITEMXH(T, KY, S, F) ST_VARIANT(T, KY, S, F, false, false, 48, 2)
 #define PAIR(T, KY, S, F) ST_VARIANT(T, KY, S, F, false, true, 0, 1)
 #define BILI(T, KY, S, F) ST_VARIANT(T, KY, S, F, true, false, 0, 1)
-const Variant kVarF32[] = {ITEMH(float, 16, 2, 16), ITEM(float, 16, 2, 16), ITEM(float, 16, 3, 12),
-                           ITEM(float, 16, 4, 8), ITEMH(float, 16, 4, 8), NEAR(float, 16, 8, 4),
-                           NEAR(float, 24, 6, 4), PAIR(float, 8, 8, 4), ITEMXH(float, 8, 2, 16),
-                           ITEMX(float, 8, 2, 16)};
+// (the first is the default; a two-velocity variant whose boxes do not hold
+// a field's motion runs as the first single-velocity one)
+const Variant kVarF32[] = {ITEMX(float, 8, 2, 16), ITEMH(float, 16, 2, 16), ITEM(float, 16, 2, 16),
+                           ITEM(float, 16, 3, 12), ITEM(float, 16, 4, 8), ITEMH(float, 16, 4, 8),
+                           NEAR(float, 16, 8, 4), NEAR(float, 24, 6, 4), PAIR(float, 8, 8, 4),
+                           ITEMXH(float, 8, 2, 16)};
 const Variant kVarF16[] = {ITEMH(__half, 16, 2, 16), ITEM(__half, 16, 2, 16),
                            NEAR(__half, 16, 8, 4), PAIR(__half, 8, 8, 4)};
 const Variant kVarBF16[] = {ITEMH(__nv_bfloat16, 16, 2, 16), ITEM(__nv_bfloat16, 16, 2, 16),
@@ -1190,6 +1192,14 @@ const Variant* variants_for(int storage, bool bl, int* count) {
   ST_LIST(kVarF32);
 }
 #undef ST_LIST
+
+// The variant that runs in place of a two-velocity one whose boxes do not
+// hold the motion: the first single-velocity one of the list.
+int single_velocity_fallback(const Variant* vars, int n) {
+  for (int v = 0; v < n; ++v)
+    if (vars[v].xpw == 1) return v;
+  return 0;
+}
 
 // TMA box width of a variant (elements)
 int box_w_of(const Variant& v, int storage) {
@@ -1335,7 +1345,8 @@ const char* fast_variant_name(const FastPlan* fp, int storage) {
   int n = 0;
   const Variant* vars = variants_for(storage, fp && fp->bl, &n);
   int v = fp ? fp->variant : -1;
-  if (v >= 0 && v < n && vars[v].xpw > 1 && !fp->fits_x2) v = 0;  // as the launch runs it
+  if (v >= 0 && v < n && vars[v].xpw > 1 && !fp->fits_x2)
+    v = single_velocity_fallback(vars, n);  // as the launch runs it
   return v >= 0 && v < n ? vars[v].name : "?";
 }
 void fast_set_variant(FastPlan* fp, int v) {
@@ -1501,7 +1512,7 @@ static const Variant* stage_maps(const FieldDev* fds, FastPlan* const* fps, int 
   int vi = fp0->variant < nvar ? fp0->variant : 0;
   // a two-velocity variant needs every field's motion within its boxes
   for (int i = 0; i < n && vars[vi].xpw > 1; ++i)
-    if (!fps[i]->fits_x2) vi = 0;
+    if (!fps[i]->fits_x2) vi = single_velocity_fallback(vars, nvar);
   const Variant& var = vars[vi];
   const int boxh = var.ky + 3 + (fp0->bl ? 1 : 0);
   const int boxw = box_w_of(var, fds[0].storage);

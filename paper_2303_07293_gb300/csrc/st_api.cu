@@ -368,7 +368,7 @@ st_status device_search(st_plan_t* p, const float* const* d_frames, const double
       } else {
         // the variants are timed on the field's frames as the search reads them
         L += normalize_field(p, tune_fi, d_frames[tune_fi]);
-        L += fast_autotune(fds[tune_fi], tp.fast, 8ll * p->sms, p->d_pend, p->pend_cap,
+        L += fast_autotune(fds[tune_fi], tp.fast, 64ll * p->sms, p->d_pend, p->pend_cap,
                            p->d_ctr, p->s);
         tune_store(p->tune_cache, key, fast_get_variant(tp.fast));
       }

@@ -106,12 +106,14 @@ def test_two_velocity_bodies_add_each_velocitys_window_pair_m_plus_c():
         lines, n_acc = g.item_loop_x2(ky, frames, row_bytes, stages, warps)
         assert n_acc == 2 * 4 * kh
         text = "\n".join(lines)
-        # the word: 18 bits of ring offset, the second column's offset from
-        # the first plus 16 in bits 18..22, the body index from bit 24
+        # the frame's four words (body index, the two windows' ring offsets,
+        # unused), the next frame's read ahead in one vector load
         head = text.split("SLOOP:\n", 1)[1].split("BTT:", 1)[0]
-        for ln in ("and.b32 sa, sw, 262143;", "shr.u32 sd, sw, 18;", "and.b32 sd, sd, 31;",
-                   "mad.lo.u32 sb, sd, 4, sa;", "sub.u32 sb, sb, 64;", "shr.u32 sid, sw, 24;"):
-            assert ln in head.splitlines(), ln
+        assert head.splitlines()[0] == "ld.shared.v4.u32 {snid, sna, snb, sw}, [swp+16];"
+        nxt = text.split("SNEXT:\n", 1)[1].splitlines()[:4]
+        assert nxt[0] == "mov.u32 sid, snid;" and nxt[3] == "add.u32 swp, swp, 16;"
+        assert re.fullmatch(r"add\.u32 sa, sna, %\d+;", nxt[1])
+        assert re.fullmatch(r"add\.u32 sb, snb, %\d+;", nxt[2])
         targets = text.split("BTT: .branchtargets ", 1)[1].split(";", 1)[0].split(", ")
         assert targets == [f"BT{b}" for b in range(32)]
         for b in range(32):

@@ -26,7 +26,7 @@ def st():
 
 
 VARIANTS = [0, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11]  # plan default and every FP32 register-window variant
-X2_TILES = (10, 11)  # two x-velocities a thread (16 or 8 consumer warps)
+X2_TILES = (2, 11)  # two x-velocities a thread (8 or 16 consumer warps)
 
 
 def dev(a):
