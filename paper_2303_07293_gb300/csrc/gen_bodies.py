@@ -182,17 +182,20 @@ def item_loop(ky, frames, row_bytes, stages, warps, dtype="f32", wait_ns=2000000
 
 
 # two x-velocities a thread (rows per thread, frames per stage, box row bytes,
-# ring stages, consumer warps): 32 accumulator pairs, as for 16 rows; the
-# boxes of 16 x-velocities are 48 FP32 wide (192 B rows)
-ITEMS_X2 = ((8, 16, 192, 2, 8), (8, 16, 192, 2, 16))
+# ring stages, consumer warps, storage): 32 accumulator pairs, as for 16
+# rows; the boxes of 16 x-velocities are 48 FP32 (192 B rows) or 56 16-bit
+# values (112 B rows) wide
+ITEMS_X2 = ((8, 16, 192, 2, 8, "f32"), (8, 16, 192, 2, 16, "f32"),
+            (8, 16, 112, 2, 8, "f16"), (8, 16, 112, 2, 8, "bf16"))
 
 
-def pattern_body_x2(p, ky, row_bytes, same, preloaded=()):
+def pattern_body_x2(p, ky, row_bytes, same, dtype="f32", preloaded=()):
     """Body of pattern p for a thread with two x-velocities (accumulator pair
     (x, j, m) is operand x*4*ky/2 + j*ky/2 + m; window pairs (q, q + ky/2)).
     same: both x-velocities read the window at sa, each pair feeding both
     velocities' accumulators; otherwise x-velocity 0 reads at sa, then
     x-velocity 1 at sb."""
+    ld, cvt = DTYPES[dtype]
     kh = ky // 2
     used = {q for q in range(kh + 3) for j in range(4) if 0 <= q - pat_off(p, j) < kh}
     L = []
@@ -205,7 +208,9 @@ def pattern_body_x2(p, ky, row_bytes, same, preloaded=()):
                 continue
             for r in (q, q + kh):
                 if r not in loaded:
-                    L.append(f"ld.shared.f32 sv{r}, [{addr}+{r * row_bytes}];")
+                    L.append(ld.format(r=r, o=r * row_bytes).replace("[sa+", f"[{addr}+"))
+                    if cvt:
+                        L += cvt.format(r=r).split("\n")
                     loaded.add(r)
             L.append(f"mov.b64 sW{q}, {{sv{q}, sv{q + kh}}};")
             for xx in ((0, 1) if same else (x,)):
@@ -217,7 +222,7 @@ def pattern_body_x2(p, ky, row_bytes, same, preloaded=()):
     return L
 
 
-def item_loop_x2(ky, frames, row_bytes, stages, warps, wait_ns=2000000000):
+def item_loop_x2(ky, frames, row_bytes, stages, warps, dtype="f32", wait_ns=2000000000):
     """As item_loop, for a thread with two adjacent x-velocities.  A frame's
     words are four: the body index (the pattern id, plus 16 when the two
     x-velocities read different columns: 0..14 and 16..30; 15 and 31: no
@@ -232,7 +237,7 @@ def item_loop_x2(ky, frames, row_bytes, stages, warps, wait_ns=2000000000):
     # the stage and barrier logic of the one-velocity loop, with its
     # operands after the accumulators moved up by the extra 4*kh pairs, its
     # words four times as wide
-    single, _ = item_loop(ky, frames, row_bytes, stages, warps, wait_ns=wait_ns)
+    single, _ = item_loop(ky, frames, row_bytes, stages, warps, dtype, wait_ns=wait_ns)
     base = 4 * kh
 
     def renum(ln):
@@ -252,14 +257,17 @@ def item_loop_x2(ky, frames, row_bytes, stages, warps, wait_ns=2000000000):
                      "add.u32 swp, swp, 16;"]
     pre = [r for q in range(PRE_X2) for r in (q, q + kh)]
     L = head + ["SLOOP:", "ld.shared.v4.u32 {snid, sna, snb, sw}, [swp+16];"]
+    ld, cvt = DTYPES[dtype]
     for r in pre:
-        L.append(f"ld.shared.f32 sv{r}, [sa+{r * row_bytes}];")
+        L.append(ld.format(r=r, o=r * row_bytes))
+        if cvt:
+            L += cvt.format(r=r).split("\n")
     L += ["BTT: .branchtargets " + ", ".join(f"BT{p}" for p in range(32)) + ";",
           "brx.idx.uni sid, BTT;"]
     for same in (True, False):
         for p in range(N_PATTERNS):
             L.append(f"BT{p + (0 if same else 16)}:")
-            L += pattern_body_x2(p, ky, row_bytes, same, preloaded=pre)
+            L += pattern_body_x2(p, ky, row_bytes, same, dtype, preloaded=pre)
             L.append("bra.uni SNEXT;")
     L += ["BT15:", "BT31:"] + tail
     return L, n_acc
@@ -276,9 +284,10 @@ def render():
         for ln in lines:
             out.append(f'  "{ln}\\n\\t" \\')
         out.append("")
-    for ky, frames, row_bytes, stages, warps in ITEMS_X2:
-        lines, n_acc = item_loop_x2(ky, frames, row_bytes, stages, warps)
-        out.append(f"#define ST_ITEMX2_KY{ky}_F{frames}_R{row_bytes}_S{stages}_W{warps} \\")
+    for ky, frames, row_bytes, stages, warps, dtype in ITEMS_X2:
+        lines, n_acc = item_loop_x2(ky, frames, row_bytes, stages, warps, dtype)
+        sfx = "" if dtype == "f32" else "_" + dtype.upper()
+        out.append(f"#define ST_ITEMX2_KY{ky}_F{frames}_R{row_bytes}_S{stages}_W{warps}{sfx} \\")
         for ln in lines:
             out.append(f'  "{ln}\\n\\t" \\')
         out.append("")

@@ -407,7 +407,7 @@ __device__ __forceinline__ void tmap_acquire(const CUtensorMap* m) {
 // H: halves per CTA.  With H = 2 the CTA has 16 consumer warps and one
 // producer (one CTA per SM, 96 registers a thread): an item covers two
 // x-velocity tiles, each with its own box per frame and its own 8 warps.
-// OPT bit 5 (FP32, KY = 8, with bit 4): two adjacent x-velocities a thread,
+// OPT bit 5 (KY = 8, with bit 4): two adjacent x-velocities a thread,
 // so a half covers 16 x-velocities (two tables' tiles, one box 8 columns
 // wider); on the frames where the two velocities' columns agree one window
 // feeds both velocities' adds.
@@ -417,8 +417,8 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
   static_assert(H == 1 || !(CP || BL), "two halves are built for single-column nearest sampling");
   constexpr bool kX2 = (OPT & 32) != 0;
   constexpr int kXPW = kX2 ? 2 : 1;        // x-velocities per thread
-  static_assert(!kX2 || ((OPT & 16) != 0 && sizeof(T) == 4 && KY == 8 && !BL && !CP),
-                "two x-velocities a thread: FP32 nearest item loop, KY = 8");
+  static_assert(!kX2 || ((OPT & 16) != 0 && KY == 8 && !BL && !CP),
+                "two x-velocities a thread: nearest item loop, KY = 8");
   constexpr int kTXv = CP ? 2 * kTX : kTX;  // tile width: one or two columns per lane
   constexpr int kBoxW = Store<T>::kBoxW + (CP ? kTX : 0) + (kX2 ? kX2Wide : 0);
   constexpr int kAccN = CP ? KY : KY / 2;   // paired accumulators per y-velocity
@@ -731,7 +731,13 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
 #define ST_ITEM_ASM(NAME) \
   asm volatile(NAME ST_ITEM_OPERANDS_KY16(acc64, slot, ph, err, nst, skip, wb0, lb, fb0, eb0))
       // (two x-velocities of 8 rows: 32 accumulator pairs, as 16 rows of one)
-      if constexpr (kX2 && F == 16 && S == 2 && kCW == 8)
+      if constexpr (kX2 && !kF32 && F == 16 && S == 2 && kCW == 8 && kF16)
+        ST_ITEM_ASM(ST_ITEMX2_KY8_F16_R112_S2_W8_F16);
+      else if constexpr (kX2 && !kF32 && F == 16 && S == 2 && kCW == 8)
+        ST_ITEM_ASM(ST_ITEMX2_KY8_F16_R112_S2_W8_BF16);
+      else if constexpr (kX2 && !kF32)
+        static_assert(F == 0, "no generated 16-bit two-velocity item loop for these stages and warps");
+      else if constexpr (kX2 && F == 16 && S == 2 && kCW == 8)
         ST_ITEM_ASM(ST_ITEMX2_KY8_F16_R192_S2_W8);
       else if constexpr (kX2 && F == 16 && S == 2 && kCW == 16)
         ST_ITEM_ASM(ST_ITEMX2_KY8_F16_R192_S2_W16);
@@ -1158,10 +1164,11 @@ const Variant kVarF32[] = {ITEMX(float, 8, 2, 16), ITEMH(float, 16, 2, 16), ITEM
                            ITEM(float, 16, 3, 12), ITEM(float, 16, 4, 8), ITEMH(float, 16, 4, 8),
                            NEAR(float, 16, 8, 4), NEAR(float, 24, 6, 4), PAIR(float, 8, 8, 4),
                            ITEMXH(float, 8, 2, 16)};
-const Variant kVarF16[] = {ITEMH(__half, 16, 2, 16), ITEM(__half, 16, 2, 16),
-                           NEAR(__half, 16, 8, 4), PAIR(__half, 8, 8, 4)};
-const Variant kVarBF16[] = {ITEMH(__nv_bfloat16, 16, 2, 16), ITEM(__nv_bfloat16, 16, 2, 16),
-                            NEAR(__nv_bfloat16, 16, 8, 4), PAIR(__nv_bfloat16, 8, 8, 4)};
+const Variant kVarF16[] = {ITEMX(__half, 8, 2, 16), ITEMH(__half, 16, 2, 16),
+                           ITEM(__half, 16, 2, 16), NEAR(__half, 16, 8, 4), PAIR(__half, 8, 8, 4)};
+const Variant kVarBF16[] = {ITEMX(__nv_bfloat16, 8, 2, 16), ITEMH(__nv_bfloat16, 16, 2, 16),
+                            ITEM(__nv_bfloat16, 16, 2, 16), NEAR(__nv_bfloat16, 16, 8, 4),
+                            PAIR(__nv_bfloat16, 8, 8, 4)};
 // bilinear sampling: two window columns, one shared horizontal interpolation
 const Variant kVarBlF32[] = {BILI(float, 8, 8, 4), BILI(float, 12, 8, 4), BILI(float, 16, 6, 4)};
 const Variant kVarBlF16[] = {BILI(__half, 8, 8, 4), BILI(__half, 12, 8, 4)};
@@ -1493,10 +1500,10 @@ int fast_prepare(const FieldDev& fd, FastPlan* fp, cudaStream_t s, bool* fits) {
                            ? Store<float>::kBoxW - kTX - (fp->bl ? 1 : 0)
                            : Store<__half>::kOColMax;
   *fits = fp->h_maxes[0] <= ocol_max && fp->h_maxes[1] < kPatterns && fd.N >= 8;
-  // two x-velocities a thread: column offsets within the wider box, and below
-  // 16 so the second velocity's offset from the first fits the 5-bit field
-  fp->fits_x2 = *fits && fd.storage == ST_F32 && !fp->bl &&
-                fp->h_maxes[3] <= Store<float>::kBoxW + kX2Wide - kTX - 1;
+  // two x-velocities a thread: lane 31 + the column offset within the
+  // wider box
+  const int box_w = fd.storage == ST_F32 ? Store<float>::kBoxW : Store<__half>::kBoxW;
+  fp->fits_x2 = *fits && !fp->bl && fp->h_maxes[3] <= box_w + kX2Wide - kTX;
   return 1;
 }
 

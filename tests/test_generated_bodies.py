@@ -101,9 +101,9 @@ def test_two_velocity_bodies_add_each_velocitys_window_pair_m_plus_c():
     # sa when the body index is below 16 (the two columns agree) and at sb
     # otherwise; accumulator pair (x, j, m) is operand x*16 + j*4 + m
     g = _gen()
-    for ky, frames, row_bytes, stages, warps in g.ITEMS_X2:
+    for ky, frames, row_bytes, stages, warps, dtype in g.ITEMS_X2:
         kh = ky // 2
-        lines, n_acc = g.item_loop_x2(ky, frames, row_bytes, stages, warps)
+        lines, n_acc = g.item_loop_x2(ky, frames, row_bytes, stages, warps, dtype)
         assert n_acc == 2 * 4 * kh
         text = "\n".join(lines)
         # the frame's four words (body index, the two windows' ring offsets,
@@ -124,11 +124,24 @@ def test_two_velocity_bodies_add_each_velocitys_window_pair_m_plus_c():
                 continue
             p, same = b % 16, b < 16
             sv, sw, adds = {}, {}, {}
+            half = {}   # 16-bit registers: what they loaded
             for ln in head.splitlines() + body.splitlines():
                 mld = re.fullmatch(r"ld\.shared\.f32 sv(\d+), \[(sa|sb)\+(\d+)\];", ln)
+                m16 = re.fullmatch(r"ld\.shared\.(?:b16 sh|u16 su)(\d+), \[(sa|sb)\+(\d+)\];", ln)
+                mcv = re.fullmatch(r"cvt\.f32\.f16 sv(\d+), sh(\d+);|mov\.b32 sv(\d+), su(\d+);",
+                                   ln)
                 mmv = re.fullmatch(r"mov\.b64 sW(\d+), \{sv(\d+), sv(\d+)\};", ln)
                 madd = re.fullmatch(r"add\.rn\.f32x2 %(\d+), %(\d+), sW(\d+);", ln)
-                if mld:
+                if m16:
+                    assert dtype != "f32"
+                    half[int(m16.group(1))] = (m16.group(2), int(m16.group(3)))
+                elif mcv:
+                    assert dtype == ("f16" if mcv.group(1) else "bf16")
+                    sv[int(mcv.group(1) or mcv.group(3))] = half[int(mcv.group(2) or mcv.group(4))]
+                elif re.fullmatch(r"shl\.b32 su(\d+), su\1, 16;", ln):
+                    assert dtype == "bf16"
+                elif mld:
+                    assert dtype == "f32"
                     sv[int(mld.group(1))] = (mld.group(2), int(mld.group(3)))
                 elif mmv:
                     q, lo, hi = map(int, mmv.groups())

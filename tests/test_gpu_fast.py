@@ -136,11 +136,14 @@ def test_fast_reduced_storage_bitexact_on_rounded_frames(st, storage):
     ks = np.arange(f["nvx"] * f["nvy"], dtype=np.int32)
     oS, oC = oracle.stack_planes(rounded, t, f, ks, prec="fp32")
     ref = oracle.search(rounded, t, f, prec="fp32")
-    for tile in (0, 2, 3, 4, 5):   # 2, 3: item loop (16 or 8 warps); 5: column pairs
+    # 2: two x-velocities a thread; 3, 4: item loop (16 or 8 warps); 6: column pairs
+    for tile in (0, 2, 3, 4, 5, 6):
         with st.Plan(f, storage=storage, tile=tile) as p:
             S, Cv = p.dump_stack(0, dev(fr), t, ks)
             got = p.candidates(dev(fr), t)
             assert p.last_stack_variant(0) == 1
+            if tile == 2:
+                assert "_o48_" in p.stack_variant_name(0), p.stack_variant_name(0)
         assert np.array_equal(S.cpu().numpy(), oS.astype(np.float32)), tile
         assert np.array_equal(Cv.cpu().numpy(), oC), tile
         assert got[["x", "y", "k", "n_cov"]].tolist() == \
@@ -176,17 +179,24 @@ def test_fast_falls_back_when_motion_spans_exceed_window(st):
     assert got[["x", "y", "k"]].tolist() == ref[["x", "y", "k"]].tolist()
 
 
-def test_two_velocity_variant_falls_back_when_its_boxes_are_too_narrow(st):
+def test_two_velocity_variant_at_the_edge_of_its_box(st):
     # velocity step 0.45 over |dt| up to about 2: an 8-velocity tile's column
-    # offsets reach 8 (its box's limit), a 16-velocity tile's reach 16 (above
-    # the wider box's limit of 15)
+    # offsets reach 8 (its box's limit), a 16-velocity tile's reach 16, so
+    # lane 31 of some warp reads the last column of the wider box.  (With a
+    # uniform velocity grid a motion that fits the 8-velocity box fits the
+    # 16-velocity one; the fit check stays as a guard.)
     fr, t, f = field(15, W=128, H=40, N=24, nvx=24, nvy=6, dv=0.45, span=4.0, ref=12)
+    ks = np.arange(f["nvx"] * f["nvy"], dtype=np.int32)
+    oS, oC = oracle.stack_planes(fr, t, f, ks, prec="fp32")
     ref = oracle.search(fr, t, f, prec="fp32")
     for tile in X2_TILES:
         with st.Plan(f, tile=tile) as p:
+            S, Cv = p.dump_stack(0, dev(fr), t, ks)
             got = p.candidates(dev(fr), t)
             assert p.last_stack_variant(0) == 1, "register-window kernel not used"
-            assert "_o48_" not in p.stack_variant_name(0), p.stack_variant_name(0)
+            assert "_o48_" in p.stack_variant_name(0), p.stack_variant_name(0)
+        assert np.array_equal(S.cpu().numpy(), oS.astype(np.float32)), tile
+        assert np.array_equal(Cv.cpu().numpy(), oC), tile
         assert got[["x", "y", "k", "n_cov"]].tolist() == ref[["x", "y", "k", "n_cov"]].tolist()
 
 
