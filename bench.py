@@ -51,8 +51,8 @@ METRIC = "G pixel*frame*velocity adds/s (2048x2048x256, 801x801 grid)"
 # blank lines removed, so only a change of the code itself retires the
 # figure): reported only while the code is that one.
 STACK_TRAFFIC = {
-    ("speculoos", "f32", "nearest", "float_ky16_s2_f16_cpfalse_o16_h2"):
-        (44.875459584e9 + 349.950208e6, "fd8a8834fbc0"),
+    ("speculoos", "f32", "nearest", "float_ky8_s2_f16_cpfalse_o48_h1"):
+        (45.867799296e9 + 370.29248e6, "119452094ca3"),
 }
 
 

@@ -358,25 +358,31 @@ struct Item {
 __device__ __host__ __forceinline__ int super_x_of(int W, int tx) {
   return ((W + tx - 1) / tx + kSuper - 1) / kSuper;
 }
+// tiles per super-tile column: 8-row tiles stack twice as many, so a
+// super-tile covers the same pixels (and frame footprint in L2) as with
+// 16-row tiles
+__device__ __host__ __forceinline__ int super_h_of(int ky) { return ky == 8 ? 2 * kSuper : kSuper; }
 __device__ __host__ __forceinline__ int groups_of(int nA, int h) { return (nA + h - 1) / h; }
 __device__ __host__ __forceinline__ int64_t items_of(const FastField& ff, int ky, int tx,
                                                      int h) {
-  const int sy = ((ff.H + ky - 1) / ky + kSuper - 1) / kSuper;
-  return (int64_t)super_x_of(ff.W, tx) * sy * kSuper * kSuper * groups_of(ff.nA, h) * ff.nB;
+  const int sh = super_h_of(ky);
+  const int sy = ((ff.H + ky - 1) / ky + sh - 1) / sh;
+  return (int64_t)super_x_of(ff.W, tx) * sy * kSuper * sh * groups_of(ff.nA, h) * ff.nB;
 }
 __device__ __forceinline__ Item decode_item(const FastField& ff, int f, int64_t L, int ky,
                                             int tx, int h) {
   const int nAg = groups_of(ff.nA, h);
   const int nVT = nAg * ff.nB;
   const int super_x = super_x_of(ff.W, tx);
-  const int sub = (int)(L % (kSuper * kSuper));
-  const int64_t rest = L / (kSuper * kSuper);
+  const int sh = super_h_of(ky);
+  const int sub = (int)(L % (kSuper * sh));
+  const int64_t rest = L / (kSuper * sh);
   const int vt = (int)(rest % nVT);
   const int stile = (int)(rest / nVT);
   Item it;
   it.f = f;
   it.X0 = ((stile % super_x) * kSuper + sub % kSuper) * tx;
-  it.Y0 = ((stile / super_x) * kSuper + sub / kSuper) * ky;
+  it.Y0 = ((stile / super_x) * sh + sub / kSuper) * ky;
   it.A = vt % nAg;
   it.B = vt / nAg;
   return it;
@@ -604,7 +610,9 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
         const uint32_t idv = cur.valid ? cur.id : (unsigned)kNoop;
 #pragma unroll
         for (int k = lane; k < F * kCW; k += 32) {
-          const int fi = k / kCW, w = k % kCW, h = w / kXV, wl = w % kXV;
+          // lanes take consecutive word groups (frame fastest, as stored):
+          // a warp's stores are conflict-free
+          const int fi = k % F, w = k / F, h = w / kXV, wl = w % kXV;
           const int src = h * F + fi;
           const uint32_t a0 = __shfl_sync(0xffffffffu, oc0, src);
           const uint32_t a1 = __shfl_sync(0xffffffffu, oc1, src);
@@ -628,7 +636,7 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
         const uint32_t idv = cur.valid ? cur.id : (unsigned)kNoop;
 #pragma unroll
         for (int k = lane; k < F * kCW; k += 32) {
-          const int fi = k / kCW, w = k % kCW, h = w / kXV;
+          const int fi = k % F, w = k / F, h = w / kXV;  // consecutive words
           const uint32_t o = __shfl_sync(0xffffffffu, ocw, h * F + fi);
           const uint32_t id = __shfl_sync(0xffffffffu, idv, h * F + fi);
           const uint32_t oc = id == (unsigned)kNoop ? 0u : (o >> (4 * (w % kXV))) & 15u;
