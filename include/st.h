@@ -300,7 +300,8 @@ int32_t st_last_stack_variant(const st_plan_t* plan, int32_t field);
 
 /* Name of the stack kernel field f used in the last search on this plan:
  * "direct-gather", the register-window variant's name (storage type, rows
- * per thread, ring stages, frames per stage, column pairs, code options,
+ * per thread, ring stages, frames per stage, column pairs, code options:
+ * o16 the generated item loop, o48 the same with two x-velocities a thread;
  * x-velocity tiles per block), or "?" before any search.  The string is
  * static (owned by the library). */
 const char* st_stack_variant_name(const st_plan_t* plan, int32_t field);

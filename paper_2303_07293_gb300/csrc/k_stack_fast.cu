@@ -396,19 +396,20 @@ __device__ __forceinline__ void tmap_acquire(const CUtensorMap* m) {
 }
 
 // Persistent kernel over every item of every field of the launch (BL:
-// bilinear sampling).  Warp 8 is the producer: it takes the next item from
+// bilinear sampling).  The last warp is the producer: it takes the next item from
 // the launch's work counter (dynamic, in the fields' longest-first order),
 // publishes the item in a ring of kItemSlots shared-memory slots, and runs
 // ahead in stages of F frames (an item's frames are padded to whole stages
 // with no-op frames, which have no copy): its lanes fetch the per-frame table
 // entries, issue the TMA copies of a stage in parallel and publish the
 // frames' column offsets, pattern ids (and bilinear fractions) and each
-// item's count of fully-inside frames in shared memory.  Warps 0..7 consume.
+// item's count of fully-inside frames in shared memory.  The other 8 (or,
+// with two halves, 16) warps consume.
 // A ring of S stages runs continuously across items and fields; when the
 // work runs out the producer publishes an end item.  Every wait is bounded.
-// OPT (nearest FP32 sampling): bit 4 runs every stage of an item in one
-// generated PTX block (st_bodies.inc): per frame, the warp's word from the
-// producer and an indexed branch into the pattern's body.  Otherwise a
+// OPT (nearest sampling): bit 4 runs every stage of an item in one
+// generated PTX block (st_bodies.inc): per frame, the warp's word(s) from
+// the producer and an indexed branch into the pattern's body.  Otherwise a
 // switch on the pattern id selects a C++ body.
 // H: halves per CTA.  With H = 2 the CTA has 16 consumer warps and one
 // producer (one CTA per SM, 96 registers a thread): an item covers two
@@ -1113,10 +1114,9 @@ __device__ __forceinline__ void stack_fast_body(const FastArgs& p) {
   }
 }
 
-// Kernels: one CTA of 9 warps (two per SM for KY <= 16, 96 registers a
-// thread), or, with two halves, one CTA of 17 warps per SM at 112 registers
-// (17 warps x 32 threads x 112 registers, counted in warp pairs, fill the
-// 64 K register file).
+// Kernels: one CTA of 9 warps (two per SM for KY <= 16), or, with two
+// halves, one CTA of 17 warps per SM; either way 96 registers a thread (the
+// 5 warps of the fullest SM sub-partition share its 16 K registers).
 template <typename T, int KY, int S, int F, bool DUMP, bool BL, bool CP, int OPT, int H>
 __global__ void __launch_bounds__(32 * (kXV + 1), KY <= 16 ? 2 : 1)
     k_stack_fast(const __grid_constant__ FastArgs p) {
